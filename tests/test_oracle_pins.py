@@ -1,0 +1,463 @@
+"""Pins of the FP64 oracle to facts fixed by the paper and by the mathematics.
+
+Each test ties one part of the oracle to something other than the oracle
+itself: a table or value the paper prints (``tests/golden/``), a closed form
+the paper states or that follows exactly from Eq. 1, an exact invariant, or a
+symmetry of the lattice.  They are chosen so that a plausible slip (a dropped
+(1 - n_s) factor, a wrong bounce-back index, a sign in a force, a swapped
+weight, a wrong relaxation time) fails at least one of them.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+CS2 = 1.0 / 3.0
+
+
+def _golden(name):
+    rows = []
+    with open(os.path.join(GOLDEN, name)) as fh:
+        for line in fh:
+            line = line.split("#")[0].strip()
+            if line:
+                rows.append([float(v) for v in line.split()])
+    return np.array(rows)
+
+
+def _momentum(f):
+    """Total momentum density sum_sigma sum_i f c_i at every node -> [3,...]."""
+    c, _, _ = oracle.lattice()
+    return np.einsum("sizyx,id->dzyx", f, c.astype(np.float64))
+
+
+# --------------------------------------------------------------------------
+# Lattice (Eq. A.8) and equilibrium (Eq. A.3)
+# --------------------------------------------------------------------------
+
+def test_velocity_set_is_the_printed_eq_A8():
+    table = _golden("d3q19_velocity_set_eqA8.txt").astype(int)
+    c, w, opp = oracle.lattice()
+    assert np.array_equal(table[:, 0], np.arange(19))
+    assert np.array_equal(table[:, 1:], c)
+    n2 = (c * c).sum(1)
+    expect_w = np.where(n2 == 0, 1 / 3, np.where(n2 == 1, 1 / 18, 1 / 36))
+    assert np.allclose(w, expect_w, rtol=0, atol=1e-17)
+    for i in range(19):
+        assert np.array_equal(c[opp[i]], -c[i])
+
+
+def test_lattice_isotropy_moments():
+    """sum w = 1, sum w c = 0, sum w c c = cs2 I, fourth moment isotropic:
+    the properties that make Eq. A.3 recover Navier-Stokes (Appendix A)."""
+    c, w, _ = oracle.lattice()
+    c = c.astype(np.float64)
+    assert abs(w.sum() - 1) < 1e-15
+    assert np.abs(np.einsum("i,id->d", w, c)).max() < 1e-16
+    assert np.allclose(np.einsum("i,ia,ib->ab", w, c, c), CS2 * np.eye(3),
+                       atol=1e-16)
+    d = np.eye(3)
+    iso = CS2 ** 2 * (np.einsum("ab,cd->abcd", d, d)
+                      + np.einsum("ac,bd->abcd", d, d)
+                      + np.einsum("ad,bc->abcd", d, d))
+    m4 = np.einsum("i,ia,ib,ic,id->abcd", w, c, c, c, c)
+    assert np.allclose(m4, iso, atol=1e-16)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_equilibrium_moments(seed):
+    """Eq. A.3 has density rho, momentum rho u and second moment
+    rho (cs2 I + u u) exactly (a dropped or mis-scaled term breaks one)."""
+    rng = np.random.default_rng(seed)
+    rho = rng.uniform(0.01, 2.0)
+    u = rng.uniform(-0.1, 0.1, 3)
+    c, _, _ = oracle.lattice()
+    c = c.astype(np.float64)
+    fe = oracle.feq(rho, u)
+    assert abs(fe.sum() - rho) < 1e-14
+    assert np.allclose(fe @ c, rho * u, atol=1e-15)
+    assert np.allclose(np.einsum("i,ia,ib->ab", fe, c, c),
+                       rho * (CS2 * np.eye(3) + np.outer(u, u)), atol=1e-15)
+
+
+# --------------------------------------------------------------------------
+# Exact consequences of Eq. 1 on uniform states
+# --------------------------------------------------------------------------
+
+def _uniform_sim(shape, ns, tau, G, F, rho=(0.7, 0.3), u=((0, 0, 0), (0, 0, 0)),
+                 gads=0.0):
+    nz, ny, nx = shape
+    p = oracle.Params(nx, ny, nz, tau=tau, G=G, Fext=F)
+    s = oracle.Sim(p, np.full(shape, ns), np.full(shape, gads))
+    f = np.zeros((2, 19) + shape)
+    for sg in range(2):
+        f[sg] = oracle.feq(rho[sg], np.array(u[sg], float))[:, None, None, None]
+    s.set_populations(f)
+    return s
+
+
+@pytest.mark.parametrize("ns,tau", [(0.05, (0.8, 1.3)), (0.3, (1.0, 1.0)),
+                                    (0.5, (0.6, 1.7)), (0.77, (1.2, 0.9)),
+                                    (0.999, (1.0, 2.0))])
+def test_exact_darcy_recurrence(ns, tau):
+    """Uniform medium, uniform densities: F_inter = F_ads = 0 and summing
+    Eq. 1 over sigma and i gives J' = (1 - 2 n_s) J + (1 - n_s) F exactly for
+    the mixture momentum J (the u' of Eq. 6 cancels), so
+    J_n = J* + (1 - 2 n_s)^n (J_0 - J*),  J* = (1 - n_s) F / (2 n_s), and
+    rho u_macro = (1 - n_s)(J + F/2) (Eq. 7), whose limit is the Darcy
+    permeability of Eq. 2: k = nu (1 - n_s) / (2 n_s)."""
+    F = np.array([1e-5, -2e-5, 3e-6])
+    u0 = ((0.01, -0.02, 0.005), (-0.03, 0.01, 0.0))
+    s = _uniform_sim((3, 2, 4), ns, tau, 1.75, tuple(F), u=u0, gads=0.2)
+    J0 = _momentum(s.f)[:, 0, 0, 0]
+    Jstar = (1 - ns) * F / (2 * ns)
+    for n in (1, 2, 7, 40):
+        s.step(n - (s.t if s.t else 0))
+        J = _momentum(s.f)[:, 0, 0, 0]
+        expect = Jstar + (1 - 2 * ns) ** n * (J0 - Jstar)
+        assert np.allclose(J, expect, rtol=1e-11, atol=1e-17), (n, J, expect)
+        fl = s.fields()
+        rho_u = fl["u"][:, 0, 0, 0] * (fl["rho_a"][0, 0, 0] + fl["rho_b"][0, 0, 0])
+        assert np.allclose(rho_u, (1 - ns) * (expect + F / 2), rtol=1e-11,
+                           atol=1e-17)
+
+
+@pytest.mark.parametrize("ns", [0.1, 0.5, 0.9])
+def test_permeability_eq2(ns):
+    """Eq. 8 applied to the converged uniform run equals Eq. 2 (Sec. 3.1)."""
+    F = 1e-5
+    tau = 1.0
+    nu = CS2 * (tau - 0.5)
+    s = _uniform_sim((2, 2, 2), ns, (tau, tau), 0.0, (F, 0.0, 0.0),
+                     rho=(0.99, 0.01))
+    s.step(300)
+    fl = s.fields()
+    rho_u = (fl["u"][0] * (fl["rho_a"] + fl["rho_b"])).mean()
+    k = nu * rho_u / F
+    assert abs(k - (1 - ns) / (2 * ns) * nu) < 1e-10 * k
+
+
+def test_rest_state_is_fixed_point():
+    """No force and no flow: Eq. 1 maps f^eq(rho, 0) to itself."""
+    s = _uniform_sim((3, 3, 3), 0.4, (0.9, 1.1), 1.75, (0, 0, 0), gads=0.3)
+    f0 = s.f.copy()
+    s.step(5)
+    assert np.abs(s.f - f0).max() < 1e-15
+
+
+# --------------------------------------------------------------------------
+# Invariants of Eq. 1 on random states
+# --------------------------------------------------------------------------
+
+def _random_sim(seed, shape=(5, 4, 7), G=1.75, F=(2e-5, -1e-5, 3e-5),
+                tau=(0.8, 1.3), ns_choice=None):
+    rng = np.random.default_rng(seed)
+    nz, ny, nx = shape
+    ns = rng.uniform(0, 1, shape)
+    ns.flat[::5] = 0.0
+    ns.flat[::7] = 1.0
+    if ns_choice is not None:
+        ns = np.full(shape, ns_choice)
+    gads = rng.uniform(-0.3, 0.3, shape)
+    p = oracle.Params(nx, ny, nz, tau=tau, G=G, Fext=F)
+    s = oracle.Sim(p, ns, gads)
+    _, w, _ = oracle.lattice()
+    base = np.array([0.8, 0.2])[:, None, None, None, None] * \
+        w[None, :, None, None, None]
+    f = base * rng.uniform(0.7, 1.3, (2, 19) + shape)
+    s.set_populations(f)
+    return s
+
+
+@pytest.mark.parametrize("seed", [3, 4])
+def test_component_mass_conserved(seed):
+    """Sum_i of the right-hand side of Eq. 1 is rho_sigma at every node and
+    streaming permutes populations, so each component's mass is invariant in
+    a closed periodic lattice."""
+    s = _random_sim(seed)
+    m0 = s.observables()["mass"]
+    s.step(60)
+    m1 = s.observables()["mass"]
+    assert np.allclose(m1, m0, rtol=1e-13, atol=0)
+
+
+def test_full_bounce_back_has_period_two():
+    """n_s = 1 everywhere is pure bounce-back (Appendix A): f(t+2) = f(t)
+    bit for bit, f(t+1) != f(t)."""
+    s = _random_sim(5, ns_choice=1.0)
+    f0 = s.f.copy()
+    s.step(1)
+    assert np.abs(s.f - f0).max() > 1e-3
+    s.step(1)
+    assert np.array_equal(s.f, f0)
+
+
+def test_uniform_medium_adhesion_vanishes():
+    """With uniform n_s and uniform G_ads the stencil of Eq. 4 sums to zero,
+    so the result does not depend on G_ads (the mechanism behind the paper's
+    finding that gamma is independent of G_ads, Sec. 3.3)."""
+    out = []
+    for g in (0.0, 0.25):
+        s = _random_sim(6, ns_choice=0.3)
+        s.gads2[...] = g
+        s.step(15)
+        out.append(s.f.copy())
+    assert np.abs(out[0] - out[1]).max() < 1e-15
+
+
+def test_rotation_and_mirror_symmetry():
+    """A quarter turn about z and the mirror x -> -x map the lattice onto
+    itself; the densities of the transformed run are the transformed
+    densities (pins the velocity table, the stencil signs and the
+    bounce-back index together)."""
+    rng = np.random.default_rng(7)
+    shape = (4, 6, 6)
+    ns = rng.uniform(0, 1, shape)
+    gads = rng.uniform(-0.3, 0.3, shape)
+    ra = rng.uniform(0.05, 1.0, shape)
+    rb = rng.uniform(0.05, 1.0, shape)
+
+    def run(ns, gads, ra, rb):
+        p = oracle.Params(shape[2], shape[1], shape[0], tau=(0.9, 1.2), G=1.5)
+        s = oracle.Sim(p, ns, gads)
+        s.init_equilibrium(ra, rb)
+        s.step(12)
+        fl = s.fields()
+        return fl["rho_a"], fl["rho_b"]
+
+    base = run(ns, gads, ra, rb)
+    rot = lambda a: np.ascontiguousarray(np.rot90(a, 1, axes=(1, 2)))
+    mir = lambda a: np.ascontiguousarray(a[:, :, ::-1])
+    for T in (rot, mir):
+        got = run(T(ns), T(gads), T(ra), T(rb))
+        for g, b in zip(got, base):
+            assert np.abs(g - T(b)).max() < 1e-13
+
+
+def test_component_swap_symmetry():
+    """Relabelling fluid 1 <-> fluid 2 together with G_ads,2 -> -G_ads,2 and
+    tau_1 <-> tau_2 swaps the two density fields (Eqs. 3-6 are symmetric in
+    sigma once G_ads,1 = -G_ads,2, Table 1)."""
+    rng = np.random.default_rng(8)
+    shape = (3, 5, 6)
+    ns = rng.uniform(0, 1, shape)
+    gads = rng.uniform(-0.3, 0.3, shape)
+    ra = rng.uniform(0.05, 1.0, shape)
+    rb = rng.uniform(0.05, 1.0, shape)
+
+    def run(gads, ra, rb, tau):
+        p = oracle.Params(shape[2], shape[1], shape[0], tau=tau, G=1.75,
+                          Fext=(1e-4, 0, -2e-4))
+        s = oracle.Sim(p, ns, gads)
+        s.init_equilibrium(ra, rb)
+        s.step(10)
+        fl = s.fields()
+        return fl["rho_a"], fl["rho_b"]
+
+    a1, b1 = run(gads, ra, rb, (0.8, 1.4))
+    a2, b2 = run(-gads, rb, ra, (1.4, 0.8))
+    assert np.abs(a1 - b2).max() < 1e-13
+    assert np.abs(b1 - a2).max() < 1e-13
+
+
+# --------------------------------------------------------------------------
+# Textbook special case: LBGK shear wave (Appendix A, Eq. A.1)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("tau", [0.8, 1.4])
+def test_shear_wave_viscosity(tau):
+    """n_s = 0, G = 0: Eq. 1 is LBGK (Eq. A.1) with nu = cs2 (tau - 1/2); a
+    shear wave u_y = U sin(2 pi x / L) decays as exp(-nu k^2 t)."""
+    L = 64
+    U = 1e-4
+    nu = CS2 * (tau - 0.5)
+    p = oracle.Params(L, 1, 1, tau=(tau, tau), G=0.0)
+    s = oracle.Sim(p, np.zeros((1, 1, L)))
+    f = np.zeros((2, 19, 1, 1, L))
+    for x in range(L):
+        u = np.array([0.0, U * math.sin(2 * math.pi * x / L), 0.0])
+        f[0, :, 0, 0, x] = oracle.feq(0.6, u)
+        f[1, :, 0, 0, x] = oracle.feq(0.4, u)
+    s.set_populations(f)
+    k = 2 * math.pi / L
+    T = int(round(math.log(2) / (nu * k * k)))   # one half-life
+    s.step(T)
+    uy = s.fields()["u"][1, 0, 0]
+    amp = 2 / L * (uy * np.sin(k * np.arange(L))).sum()
+    # O(k^2) lattice correction to the continuum rate: 0.3 % at k = 2 pi / 64
+    assert abs(amp / (U * math.exp(-nu * k * k * T)) - 1) < 1e-2
+
+
+# --------------------------------------------------------------------------
+# Darcy-Brinkman benchmarks of Sec. 3.2 and Table C.1
+# --------------------------------------------------------------------------
+
+def _open_boundary_umax(ns_right, steps):
+    H = 100
+    F = 1e-6
+    ns = np.zeros((1, 1, H))
+    ns[..., : H // 2 + 1] = 0.9          # x in [0, H/2]
+    ns[..., H // 2 + 1:] = ns_right      # x in ]H/2, H]
+    p = oracle.Params(H, 1, 1, tau=(1.0, 1.0), G=0.0, Fext=(0.0, F, 0.0))
+    s = oracle.Sim(p, ns)
+    s.init_equilibrium(np.full(ns.shape, 0.99), np.full(ns.shape, 0.01))
+    s.step(steps)
+    return s.fields()["u"][1, 0, 0].max()
+
+
+def _eq13_right_centre(ns_l, ns_r, H=100, F=1e-6, nu=1 / 6):
+    """Eq. 13b with Table 2's parameters, at the centre x = 3H/4."""
+    kl = (1 - ns_l) / (2 * ns_l) * nu
+    kr = (1 - ns_r) / (2 * ns_r) * nu
+    U0r = kr * F / nu
+    pr = kl / kr
+    qr = math.sqrt(ns_r / ns_l)
+    rl = math.sqrt(2 * ns_l / nu)
+    rr = math.sqrt(2 * ns_r / nu)
+    coth = lambda v: math.cosh(v) / math.sinh(v)
+    return U0r * (1 + (pr - 1) / (math.sinh(rr * H / 4)
+                                  * (qr * coth(rl * H / 4) + coth(rr * H / 4))))
+
+
+@pytest.mark.parametrize("row", [1, 2, 3, 4])
+def test_open_boundary_umax_table(row):
+    """Table C.1: u_max of the two-layer open-boundary flow (Sec. 3.2)."""
+    ns_r, umax = _golden("open_boundary_umax_tableC1.txt")[row]
+    got = _open_boundary_umax(ns_r, 3000)
+    assert abs(got / umax - 1) < 1e-3
+
+
+def test_open_boundary_brinkman_row_follows_eq13():
+    """Row n_s,right = 0.001 of Table C.1 prints 4.732e-4, but Eq. 13b with
+    Table 2's parameters gives 4.372e-4 at the layer centre; the oracle is
+    held to Eq. 13b (2 %), the closed form the paper says the runs match."""
+    got = _open_boundary_umax(0.001, 20000)
+    assert abs(got / _eq13_right_centre(0.9, 0.001) - 1) < 0.02
+
+
+@pytest.mark.parametrize("ns", [0.001, 0.01, 0.1, 0.5, 0.9])
+def test_poiseuille_with_bounce_back_walls(ns):
+    """Sec. 3.2 paragraph 1: walls are n_s = 1 cells (x = 0 and x = H+1),
+    fluid cells 1..H sit at x_a = i - 1/2 from the wall; the profile is
+    Eq. 11.  The centre value matches to 1e-6 where the centre is Darcy-like
+    (n_s >= 0.1) and to 1e-3 otherwise; the whole
+    profile to 1 % of u_max in the Brinkman regime (n_s <= 0.1), where the
+    paper reports excellent agreement."""
+    H, F, nu = 50, 1e-5, 1 / 6
+    steps = {0.001: 30000, 0.01: 8000}.get(ns, 2500)
+    nsf = np.full((1, 1, H + 2), ns)
+    nsf[..., 0] = nsf[..., -1] = 1.0
+    p = oracle.Params(H + 2, 1, 1, tau=(1.0, 1.0), G=0.0, Fext=(0.0, F, 0.0))
+    s = oracle.Sim(p, nsf)
+    s.init_equilibrium(np.full(nsf.shape, 0.99), np.full(nsf.shape, 0.01))
+    s.step(steps)
+    u = s.fields()["u"][1, 0, 0, 1:-1]
+    k = (1 - ns) / (2 * ns) * nu
+    r = math.sqrt(2 * ns / nu)
+    xa = np.arange(1, H + 1) - 0.5
+    ua = F * k / nu * (1 - np.cosh(r * (xa - H / 2)) / np.cosh(r * H / 2))
+    assert abs(u[H // 2] / ua[H // 2] - 1) < (1e-6 if ns >= 0.1 else 1e-3)
+    if ns <= 0.1:
+        assert np.abs(u - ua).max() < 0.01 * ua.max()
+
+
+# --------------------------------------------------------------------------
+# Bubble test (Sec. 3.3): Laplace law, gamma(G), independence of n_s
+# --------------------------------------------------------------------------
+
+def _coexistence(G):
+    """Bulk densities of a flat interface at rest (1D run of the oracle)."""
+    H = 48
+    x = np.arange(H)
+    inside = (x >= H // 4) & (x < 3 * H // 4)
+    p = oracle.Params(H, 1, 1, tau=(1.0, 1.0), G=G)
+    s = oracle.Sim(p, np.zeros((1, 1, H)))
+    s.init_equilibrium(np.where(inside, 0.99, 0.01)[None, None],
+                       np.where(inside, 0.01, 0.99)[None, None])
+    s.step(6000)
+    fl = s.fields()
+    return fl["rho_a"][0, 0, H // 2], fl["rho_b"][0, 0, H // 2]
+
+
+def _bubble_gamma(G, ns, steps, H=64, R=14):
+    hi, lo = _coexistence(G)
+    yy, xx = np.meshgrid(np.arange(H), np.arange(H), indexing="ij")
+    r = np.hypot(xx - H / 2 + 0.5, yy - H / 2 + 0.5)
+    inside = r < R
+    p = oracle.Params(H, H, 1, tau=(1.0, 1.0), G=G)
+    s = oracle.Sim(p, np.full((1, H, H), ns))
+    s.init_equilibrium(np.where(inside, hi, lo)[None],
+                       np.where(inside, lo, hi)[None])
+    s.step(steps)
+    fl = s.fields()
+    a, pr = fl["rho_a"][0], fl["p"][0]
+    area = ((a - a.min()) / (a.max() - a.min())).sum()
+    Req = math.sqrt(area / math.pi)
+    dp = pr[r < Req / 2].mean() - pr[r > Req + 8].mean()
+    return dp * Req          # 2D Laplace law: gamma = dp R (Sec. 3.3)
+
+
+@pytest.mark.slow
+def test_laplace_gamma_vs_G_and_ns():
+    """gamma = dp R (Sec. 3.3) on a 64 x 64 bubble of radius 14.  The paper
+    notes that gamma measured in small domains comes out high and converges
+    to 0.077 only for H >= 100; at H = 64 this measurement reads 7-13 % high,
+    so the printed gamma(G) is held to 15 %, the printed ratio
+    gamma(2.0)/gamma(1.5) = 2.04 to 8 %, and gamma at n_s = 0.5 must equal
+    gamma at n_s = 0 within 1 % (the paper's central claim for the model).
+    A force of the wrong sign dissolves the bubble, a factor-2 slip in G moves
+    gamma far outside these bands."""
+    table = _golden("interfacial_tension_sec33.txt")
+    got = {G: _bubble_gamma(G, 0.0, 3000) for G in table[:, 0]}
+    for G, gam in table:
+        assert abs(got[G] / gam - 1) < 0.15, (G, got[G], gam)
+    ratio = got[2.0] / got[1.5]
+    assert abs(ratio / (0.104 / 0.051) - 1) < 0.08, ratio
+    g_half = _bubble_gamma(1.75, 0.5, 6000)
+    assert abs(g_half / got[1.75] - 1) < 0.01
+
+
+# --------------------------------------------------------------------------
+# Reservoirs and observables (Sec. 4, Eqs. 18-19, Eq. A.6)
+# --------------------------------------------------------------------------
+
+def test_reservoir_layers_and_observables():
+    """After a step the reservoir layers hold f^eq(rho_res, 0) exactly; the
+    mean pressure over a reservoir is Eq. A.6 at the prescribed densities;
+    S_1 (Eq. 19) weights each non-reservoir cell by 1 - n_s and counts it
+    when rho_1 >= 0.5."""
+    nx, ny, nz = 12, 3, 2
+    G = 1.75
+    res = {0: (4, 1.04, 0.01), 1: (4, 0.01, 0.99)}
+    p = oracle.Params(nx, ny, nz, tau=(1.0, 1.0), G=G, reservoirs=res)
+    rng = np.random.default_rng(9)
+    ns = rng.uniform(0, 1, (nz, ny, nx))
+    s = oracle.Sim(p, ns, rng.uniform(-0.2, 0.2, (nz, ny, nx)))
+    ra = np.where(np.arange(nx) < 6, 0.99, 0.01)[None, None].repeat(ny, 1).repeat(nz, 0)
+    s.init_equilibrium(ra, 1.0 - ra)
+    s.step(3)
+    for face, (L, r1, r2) in res.items():
+        xs = range(L) if face == 0 else range(nx - L, nx)
+        for x in xs:
+            assert np.array_equal(s.f[0, :, :, :, x],
+                                  np.broadcast_to(oracle.feq(r1, np.zeros(3))[:, None, None],
+                                                  (19, nz, ny)))
+            assert np.array_equal(s.f[1, :, :, :, x],
+                                  np.broadcast_to(oracle.feq(r2, np.zeros(3))[:, None, None],
+                                                  (19, nz, ny)))
+    obs = s.observables()
+    for face, (L, r1, r2) in res.items():
+        assert abs(obs["p_face"][face] - CS2 * (r1 + r2 + G * r1 * r2)) < 1e-15
+    assert all(math.isnan(v) for v in obs["p_face"][2:])
+    fl = s.fields()
+    inner = np.zeros((nz, ny, nx), bool)
+    inner[..., 4:nx - 4] = True
+    wgt = (1 - ns)[inner]
+    filled = (fl["rho_a"] >= 0.5)[inner]
+    assert abs(obs["sat1"] - wgt[filled].sum() / wgt.sum()) < 1e-14
+    assert np.allclose(obs["mass"], [fl["rho_a"].sum(), fl["rho_b"].sum()],
+                       rtol=1e-15)
