@@ -1,0 +1,372 @@
+"""Throughput benchmark of the HMCSC D3Q19 step on GB300.
+
+Workload: the synthetic 256^3 electrode-imbibition problem (Boolean model of
+solid spheres, gray binder blobs with per-blob n_s, reservoirs at x = 0 and
+x = 255, Table 1 parameters), float32 populations.  A benchmark step is one
+lattice time step over the whole domain: the density pass and the fused
+force/collide/bounce-back/stream pass.
+
+Prints one JSON line:
+  value    aggregate MLUPS (lattice node updates per second / 1e6, both
+           components) over all ranks, device-timed with CUDA events;
+  e2e      the same metric through the C ABI with host buffers: geometry and
+           density upload, the steps, and the field read-back inside the
+           timed region;
+  roofline the fused pass's algorithmic bytes per launch over its average
+           launch duration, against the measured HBM copy bandwidth;
+  cpu_baseline  the FP64 oracle on the host cores on a bounded sample.
+
+``--impl reference`` times the FP64 CPU oracle instead (rank 0 only).
+Multi-GPU (torchrun): every rank advances its own replica of the domain; no
+data crosses ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "2-comp D3Q19 MLUPS"
+UNIT = "MLUPS"
+# Algorithmic bytes per node and step (float32 storage):
+#   density pass: read 2 x 19 x 4, write 2 x 4              = 160
+#   fused pass:   read 2 x 19 x 4 + rho 8 + n_s 4 + a 4,
+#                 write 2 x 19 x 4                          = 320
+BYTES_DENSITY = 160
+BYTES_COLLIDE = 320
+FALLBACK_HBM_GBS = 6800.0
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def _kernel_sha():
+    h = hashlib.sha256()
+    for f in ("lbm_kernels.cu", "lbm_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2206_11524_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _profiled_traffic(kernel):
+    """DRAM bytes per node of `kernel` from the committed ncu summary, if the
+    summary was taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_electrode256.md")
+    if not os.path.exists(path):
+        return None
+    sha = bpn = None
+    for line in open(path):
+        if line.startswith("kernel_source_sha256_16:"):
+            sha = line.split(":", 1)[1].strip()
+        if line.startswith("dram_bytes_per_node:"):
+            bpn = float(line.split(":", 1)[1].strip())
+    if sha != _kernel_sha() or bpn is None:
+        return None
+    return bpn
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                 "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def aggregate_max(value: float, world: int) -> float:
+    """Max of a float over ranks (identity when world == 1)."""
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def cpu_oracle_mlups(case_small, budget_s: float, max_steps: int | None = None):
+    """Time the FP64 oracle on a bounded sample; returns (MLUPS, steps, s)."""
+    import oracle
+    oracle.build()
+    nz, ny, nx = case_small.shape
+    p = oracle.Params(nx, ny, nz, tau=case_small.tau, G=case_small.G,
+                      Fext=case_small.F_ext, reservoirs=case_small.reservoirs)
+    s = oracle.Sim(p, case_small.ns, case_small.gads2)
+    s.init_equilibrium(case_small.rho_a, case_small.rho_b)
+    s.step(1)                      # warm-up (page-in, thread start)
+    steps = 0
+    t0 = time.perf_counter()
+    while True:
+        s.step(1)
+        steps += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s or (max_steps and steps >= max_steps):
+            break
+    return case_small.n_nodes * steps / el / 1e6, steps, el
+
+
+def _cores():
+    n = os.environ.get("OMP_NUM_THREADS")
+    return int(n) if n else (os.cpu_count() or 1)
+
+
+def run_reference(args, world, rank):
+    """FP64 oracle on the host cores, on a 64^3 crop of the workload."""
+    if rank != 0:
+        return 0
+    from paper_2206_11524_gb300 import synth
+    small = synth.electrode((64, 64, 64))
+    for _ in range(args.warmup):
+        cpu_oracle_mlups(small, 0.0, max_steps=1)
+    t0 = time.perf_counter()
+    total_nodes = 0
+    for _ in range(args.steps):
+        _, st, _ = cpu_oracle_mlups(small, 0.0, max_steps=1)
+        total_nodes += small.n_nodes * st
+    el = time.perf_counter() - t0
+    v = total_nodes / el / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": el / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "electrode imbibition, 64^3 crop of the "
+                                   "256^3 synthetic electrode (CPU sample)",
+                       "parallelism": "host cores"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": _cores(),
+                             "kind": "oracle",
+                             "sample": "64^3 synthetic electrode, one time "
+                                       "step per benchmark step"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gpu(args, world, rank, local):
+    import numpy as np
+    import torch
+    from paper_2206_11524_gb300 import build as lib_build
+    from paper_2206_11524_gb300 import lbm, synth
+
+    lib_build.build()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    n = args.size
+    case = synth.electrode((n, n, n))
+    nz, ny, nx = case.shape
+    N = case.n_nodes
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        lat = lbm.Lattice(nx, ny, nz, tau=case.tau, G=case.G, F_ext=case.F_ext,
+                          stream=stream)
+    ctx = lat.ctx
+    lat.set_geometry(case.ns, case.gads2)
+    for face, (L, r1, r2) in case.reservoirs.items():
+        lat.set_bc(face, L, r1, r2)
+    lat.init_equilibrium(case.rho_a, case.rho_b)
+
+    for _ in range(args.warmup):
+        lbm.lbm_density(ctx)
+        lbm.lbm_collide_stream(ctx)
+    torch.cuda.synchronize()
+
+    K = args.steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    start = torch.cuda.Event(enable_timing=True)
+    stop = torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    barrier(world)
+    torch.cuda.synchronize()
+    start.record(stream)
+    for k in range(K):
+        e0, e1, e2 = ev[k]
+        e0.record(stream)
+        lbm.lbm_density(ctx)
+        e1.record(stream)
+        lbm.lbm_collide_stream(ctx)
+        e2.record(stream)
+    stop.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    ms = start.elapsed_time(stop)
+    ms_density = sum(a.elapsed_time(b) for a, b, _ in ev) / K
+    ms_collide = sum(b.elapsed_time(c) for _, b, c in ev) / K
+    ms_max = aggregate_max(ms, world)
+    value = world * N * K / (ms_max / 1e3) / 1e6
+    obs = lat.observables()
+    assert obs["nonfinite"] == 0, "non-finite densities in the benchmark run"
+
+    # End to end through the C ABI with host buffers (pinned).
+    def pinned(shape):
+        return torch.empty(shape, dtype=torch.float32, pin_memory=True).numpy()
+    h_ns, h_g = pinned(case.shape), pinned(case.shape)
+    h_ra, h_rb = pinned(case.shape), pinned(case.shape)
+    h_ns[...] = case.ns
+    h_g[...] = case.gads2
+    h_ra[...] = case.rho_a
+    h_rb[...] = case.rho_b
+    o_ra, o_rb, o_p = pinned(case.shape), pinned(case.shape), pinned(case.shape)
+    o_u = pinned((3,) + case.shape)
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    lbm.lbm_set_geometry(ctx, h_ns, h_g, N)
+    lbm.lbm_init_equilibrium(ctx, h_ra, h_rb, N)
+    lbm.lbm_step(ctx, K)
+    lbm.lbm_read_fields(ctx, o_ra, o_rb, o_u, o_p)
+    e2e_s = aggregate_max(time.perf_counter() - t0, world)
+    e2e_value = world * N * K / e2e_s / 1e6
+    h2d = 4 * 4 * N
+    d2h = 6 * 4 * N
+
+    peak, peak_kind = _peaks()
+    achieved = BYTES_COLLIDE * N / (ms_collide / 1e3) / 1e9
+    traffic_bpn = _profiled_traffic("collide_stream")
+    if rank != 0:
+        return 0
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        small = synth.electrode((64, 64, 64))
+        mlups, st, el = cpu_oracle_mlups(small, args.cpu_seconds)
+        cpu = {"value": mlups, "unit": UNIT, "cores": _cores(), "kind": "oracle",
+               "sample": f"64^3 crop-size synthetic electrode, {st} FP64 "
+                         f"time steps in {el:.1f} s"}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": K, "warmup": args.warmup, "ms_per_step": ms_max / K,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"electrode imbibition {n}^3: synthetic "
+                               "overlapping-sphere solid (n_s=1) + gray binder "
+                               "blobs (n_s~U[0.2,0.9]), reservoirs at x=0 and "
+                               f"x={n - 1}, tau=1, G=1.75, f32 storage",
+                   "nodes": N, "global_nodes": N * world,
+                   "l2": "inputs larger than L2 (working set "
+                         f"{lat.workspace.numel() / 1e9:.2f} GB)",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak,
+                     "unit": "GB/s", "frac": achieved / peak,
+                     "peak_kind": f"{peak_kind} hbm_gbs",
+                     "kernel": "k_collide_stream",
+                     "algorithmic_bytes_per_node": BYTES_COLLIDE,
+                     "traffic": (traffic_bpn * N if traffic_bpn else None)},
+        "kernels_ms": {"density": ms_density, "collide_stream": ms_collide},
+        "step_hbm_gbs": (BYTES_DENSITY + BYTES_COLLIDE) * N / (ms_max / K / 1e3) / 1e9,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d / K,
+                "d2h_bytes_per_step": d2h / K},
+        "gpu_launches": 2 * K,
+        "clocks": clk,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    lat.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--size", type=int, default=256)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    world, rank, local = _dist()
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+    return run_gpu(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,176 @@
+/*
+ * lbm.h -- C ABI of the GB300 (sm_103a) homogenized multi-component
+ * Shan-Chen lattice Boltzmann library (HMCSC, arXiv 2206.11524).
+ *
+ * One context advances one two-component D3Q19 lattice with the update of
+ * Eq. 1 (gray BGK with partial bounce-back of fraction n_s), the Shan-Chen
+ * fluid-fluid force of Eq. 3, the fluid-solid adhesion force of Eq. 4, the
+ * body-force split of Eq. 5 and the equilibrium-velocity shift of Eq. 6.
+ *
+ * Conventions for every entry point:
+ *   - Lattice size nx, ny, nz >= 1; node index n = x + nx*(y + ny*z), x
+ *     fastest.  N = nx*ny*nz.  The lattice is periodic on every axis; walls
+ *     are n_s = 1 cells (Appendix A) and open faces are density reservoirs
+ *     (lbm_set_bc, Sec. 4).
+ *   - Populations are numbered in the D3Q19 order of Eq. A.8 (direction
+ *     i + 9 is the opposite of direction i for i = 1..9); component 0 is
+ *     fluid 1, component 1 is fluid 2.
+ *   - Host arrays (float*, double*) are caller-owned and only read or written
+ *     during the call.  Device memory is never allocated by the library: the
+ *     caller passes one device workspace of lbm_workspace_bytes() bytes,
+ *     which the library carves up and never frees.  lbm_destroy frees only
+ *     the host-side context.
+ *   - Every call returns an lbm_status; nothing aborts or throws.  After an
+ *     error, lbm_last_error(ctx) holds a one-line message.
+ *   - Work is enqueued on the CUDA stream given to lbm_create.  Calls that
+ *     return host data (read_fields, reduce, get_populations, save) wait for
+ *     that stream.  A context must not be used from two threads at once.
+ */
+#ifndef HMCSC_LBM_H
+#define HMCSC_LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define LBM_API __attribute__((visibility("default")))
+#else
+#define LBM_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  LBM_OK = 0,
+  LBM_EINVAL = 1,    /* an argument is out of range or NULL             */
+  LBM_ENOMEM = 2,    /* workspace smaller than lbm_workspace_bytes()    */
+  LBM_ECUDA = 3,     /* a CUDA runtime call failed (message has detail) */
+  LBM_ENAN = 4,      /* a density became non-finite                     */
+  LBM_ETIMEOUT = 5,  /* lbm_sync: the stream did not finish in time     */
+  LBM_ESTATE = 6,    /* call out of order (e.g. step before geometry)   */
+  LBM_EINTERNAL = 7  /* a kernel reported an internal inconsistency     */
+} lbm_status;
+
+typedef enum {
+  LBM_STORAGE_F32 = 0 /* populations stored as float32 */
+} lbm_storage;
+
+/* Model parameters (names of Table 1). */
+typedef struct {
+  int32_t nx, ny, nz;
+  int32_t storage;   /* lbm_storage                                         */
+  double tau[2];     /* relaxation times tau_1, tau_2 > 1/2         (Eq. 1) */
+  double G;          /* G_inter,12 = G_inter,21                     (Eq. 3) */
+  double F_ext[3];   /* body force on the mixture, split by Eq. 5           */
+} lbm_params;
+
+/* Observables of the current state (Sec. 4, Eqs. 18-19, Eq. A.6). */
+typedef struct {
+  double mass[2];    /* sum over all nodes of rho_1 and rho_2               */
+  double sat1;       /* S_1 of Eq. 19: nodes outside every reservoir, each
+                        weighted by 1 - n_s, counted when rho_1 >= 0.5;
+                        NaN when that weight sums to zero                   */
+  double p_face[6];  /* mean pressure (Eq. A.6) over each reservoir face's
+                        layers, faces -x,+x,-y,+y,-z,+z; NaN if no reservoir.
+                        Eq. 18's Delta p = inlet mean - outlet mean.        */
+  int64_t nonfinite; /* nodes whose rho_1 or rho_2 is NaN or infinite       */
+} lbm_observables;
+
+typedef struct lbm_ctx lbm_ctx;
+
+/* Bytes of device workspace a context with these parameters needs
+ * (populations 2 x 19 x N floats, densities, geometry, output staging and
+ * reduction scratch).  Returns 0 if the parameters are invalid. */
+LBM_API size_t lbm_workspace_bytes(const lbm_params *params);
+
+/* Create a context.  d_workspace: device pointer, 256-byte aligned, at least
+ * lbm_workspace_bytes(params) bytes, owned by the caller and kept alive until
+ * lbm_destroy.  cuda_stream: a cudaStream_t (NULL = legacy default stream).
+ * The state starts unset: call lbm_set_geometry, then lbm_init_equilibrium or
+ * lbm_set_populations, before stepping.  Errors: EINVAL (bad params, NULL
+ * out), ENOMEM (workspace too small), ECUDA. */
+LBM_API lbm_status lbm_create(const lbm_params *params, void *d_workspace,
+                      size_t workspace_bytes, void *cuda_stream,
+                      lbm_ctx **out);
+
+/* Free the host context (never the workspace).  NULL is a no-op. */
+LBM_API void lbm_destroy(lbm_ctx *ctx);
+
+/* Static geometry (Sec. 2, Sec. 4): ns[N] = bounce-back fraction n_s in
+ * [0, 1] (Eq. 1), gads2[N] = G_ads,2 per node (Eq. 4; G_ads,1 = -G_ads,2,
+ * Table 1; NULL = all zero).  Host arrays, copied to the device.
+ * EINVAL if any n_s is outside [0, 1] or not finite. */
+LBM_API lbm_status lbm_set_geometry(lbm_ctx *ctx, const float *ns, const float *gads2);
+
+/* Start from rest: f_i,sigma = f^eq_i(rho_sigma, u = 0) (Eq. A.3), time 0.
+ * rho_a, rho_b: host [N], each > 0 and finite (EINVAL otherwise). */
+LBM_API lbm_status lbm_init_equilibrium(lbm_ctx *ctx, const float *rho_a,
+                                const float *rho_b);
+
+/* Set every population: f[2][19][N] (host, natural layout: f[s][i][n] is
+ * f_i,s at node n), time 0.  EINVAL if a component density is <= 0. */
+LBM_API lbm_status lbm_set_populations(lbm_ctx *ctx, const float *f);
+
+/* Copy every population of the current time step to the host, in the
+ * natural layout of lbm_set_populations.  Waits for the stream. */
+LBM_API lbm_status lbm_get_populations(lbm_ctx *ctx, float *f);
+
+/* Density reservoir on one face (Sec. 4): after every step the `layers`
+ * outermost layers of face `face` (0..5 = -x,+x,-y,+y,-z,+z) hold
+ * f^eq(rho_a / rho_b, u = 0).  layers = 0 removes it.  Where two faces'
+ * layers overlap, the higher face index wins.  May be called between steps
+ * (an inlet density ramp).  EINVAL if the layers exceed the axis length or a
+ * density is not positive. */
+LBM_API lbm_status lbm_set_bc(lbm_ctx *ctx, int face, int layers, double rho_a,
+                      double rho_b);
+
+/* Advance n_steps time steps (Eq. 1 plus the reservoirs), asynchronously on
+ * the context's stream.  Each step launches the density pass and the fused
+ * force/collide/bounce-back/stream pass.  n_steps = 0 is a no-op. */
+LBM_API lbm_status lbm_step(lbm_ctx *ctx, int n_steps);
+
+/* The two halves of one step, for callers that time or interleave them:
+ * lbm_density (rho_sigma of Eq. A.4 at every node) followed by
+ * lbm_collide_stream (Eqs. 3-6, A.3, 1 and the reservoirs) is exactly one
+ * lbm_step(ctx, 1).  lbm_collide_stream without a preceding lbm_density at
+ * the same time step is ESTATE. */
+LBM_API lbm_status lbm_density(lbm_ctx *ctx);
+LBM_API lbm_status lbm_collide_stream(lbm_ctx *ctx);
+
+/* Time steps taken since the last init / set_populations / load. */
+LBM_API int64_t lbm_time(const lbm_ctx *ctx);
+
+/* Macroscopic fields of the current state, to host arrays (any may be NULL):
+ * rho_a[N], rho_b[N] (Eq. A.4); u[3][N] = u_macro of Eq. 7 (x, y, z planes);
+ * p[N] = c_s^2 (rho + G rho_1 rho_2) (Eq. A.6).  Waits for the stream. */
+LBM_API lbm_status lbm_read_fields(lbm_ctx *ctx, float *rho_a, float *rho_b, float *u,
+                           float *p);
+
+/* Observables of the current state (FP64 accumulation, fixed summation
+ * order, so repeated calls on the same state give identical bits).  Waits
+ * for the stream.  Returns ENAN (after filling *out) if nonfinite > 0. */
+LBM_API lbm_status lbm_reduce(lbm_ctx *ctx, lbm_observables *out);
+
+/* Wait for the context's stream, polling; ETIMEOUT after timeout_s seconds
+ * (the work stays queued; the context remains usable). */
+LBM_API lbm_status lbm_sync(lbm_ctx *ctx, double timeout_s);
+
+/* Checkpoint: lbm_checkpoint_bytes() bytes hold the lattice size, storage,
+ * time step and every population in the device's own layout; lbm_load
+ * restores them into a context created with the same lattice size and
+ * storage (EINVAL otherwise, or when the header does not check).  Resuming
+ * from a checkpoint reproduces the uninterrupted run bit for bit. */
+LBM_API size_t lbm_checkpoint_bytes(const lbm_ctx *ctx);
+LBM_API lbm_status lbm_save(lbm_ctx *ctx, void *host_buf, size_t bytes);
+LBM_API lbm_status lbm_load(lbm_ctx *ctx, const void *host_buf, size_t bytes);
+
+/* Message of the last error on this context ("" if none). */
+LBM_API const char *lbm_last_error(const lbm_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HMCSC_LBM_H */

@@ -1,0 +1,464 @@
+// lbm_api.cu -- host side of the C ABI declared in include/lbm.h.
+//
+// The context owns no device memory: it carves the caller's workspace into
+// populations, densities, geometry, staging and reduction scratch, and
+// enqueues kernels on the caller's stream.
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "lbm.h"
+#include "lbm_internal.cuh"
+
+using hmcsc::kFaces;
+using hmcsc::kQ;
+using hmcsc::kRedBlocks;
+using hmcsc::kRedK;
+
+struct lbm_ctx {
+  lbm_params params;
+  hmcsc::StepParams sp;
+  hmcsc::Workspace ws;
+  cudaStream_t stream;
+  long long N;
+  int64_t t;             // time steps since the state was set
+  int64_t rho_at;        // time step of the densities in ws.rho (-1: none)
+  bool have_geometry;
+  bool have_state;
+  std::string err;
+};
+
+namespace {
+
+lbm_status fail(lbm_ctx *c, lbm_status s, const char *fmt, ...) {
+  if (c) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    c->err = buf;
+  }
+  return s;
+}
+
+lbm_status cuda_fail(lbm_ctx *c, cudaError_t e, const char *what) {
+  return fail(c, LBM_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+bool params_valid(const lbm_params *p, const char **why) {
+  if (!p) { *why = "params is NULL"; return false; }
+  if (p->nx < 1 || p->ny < 1 || p->nz < 1) { *why = "nx, ny, nz must be >= 1"; return false; }
+  const long long N = (long long)p->nx * p->ny * p->nz;
+  if (N > 2147483647LL) { *why = "nx*ny*nz must be < 2^31"; return false; }
+  if ((p->ny + 3) / 4 > 65535 || (p->nz + 1) / 2 > 65535) { *why = "ny or nz too large"; return false; }
+  if (p->storage != LBM_STORAGE_F32) { *why = "unsupported storage"; return false; }
+  for (int s = 0; s < 2; ++s)
+    if (!(p->tau[s] > 0.5) || !std::isfinite(p->tau[s])) { *why = "tau must be finite and > 1/2"; return false; }
+  if (!std::isfinite(p->G)) { *why = "G must be finite"; return false; }
+  for (int d = 0; d < 3; ++d)
+    if (!std::isfinite(p->F_ext[d])) { *why = "F_ext must be finite"; return false; }
+  return true;
+}
+
+size_t padded_stride(const lbm_ctx *c) { return (size_t)c->sp.np; }
+
+int parity(const lbm_ctx *c) { return (int)(c->t & 1); }
+
+// Checkpoint header.
+struct CkptHeader {
+  char magic[8];
+  int32_t version, storage;
+  int32_t nx, ny, nz, pad;
+  int64_t t, np;
+};
+const char kMagic[8] = {'H', 'M', 'C', 'S', 'C', 'L', 'B', '1'};
+
+lbm_status sync_stream(lbm_ctx *c, const char *what) {
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, what);
+  return LBM_OK;
+}
+
+// Upload n floats from host to a device staging plane (pageable copy).
+lbm_status upload(lbm_ctx *c, float *dst, const float *src, size_t n) {
+  cudaError_t e = cudaMemcpyAsync(dst, src, n * sizeof(float),
+                                  cudaMemcpyHostToDevice, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "host-to-device copy");
+  return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t lbm_workspace_bytes(const lbm_params *params) {
+  const char *why = nullptr;
+  if (!params_valid(params, &why)) return 0;
+  return hmcsc::workspace_bytes(params->nx, params->ny, params->nz, nullptr,
+                                nullptr);
+}
+
+lbm_status lbm_create(const lbm_params *params, void *d_workspace,
+                      size_t workspace_bytes, void *cuda_stream,
+                      lbm_ctx **out) {
+  if (!out) return LBM_EINVAL;
+  *out = nullptr;
+  const char *why = nullptr;
+  if (!params_valid(params, &why)) return LBM_EINVAL;
+  if (!d_workspace || ((uintptr_t)d_workspace & 255u)) return LBM_EINVAL;
+  const size_t need = hmcsc::workspace_bytes(params->nx, params->ny,
+                                             params->nz, nullptr, nullptr);
+  if (workspace_bytes < need) return LBM_ENOMEM;
+  lbm_ctx *c = new lbm_ctx();
+  c->params = *params;
+  c->stream = (cudaStream_t)cuda_stream;
+  c->N = (long long)params->nx * params->ny * params->nz;
+  hmcsc::workspace_bytes(params->nx, params->ny, params->nz, &c->ws,
+                         (char *)d_workspace);
+  hmcsc::StepParams &sp = c->sp;
+  sp.nx = params->nx;
+  sp.ny = params->ny;
+  sp.nz = params->nz;
+  sp.np = (c->N + 63) / 64 * 64;
+  for (int s = 0; s < 2; ++s) {
+    sp.tau[s] = (float)params->tau[s];
+    sp.omega[s] = (float)(1.0 / params->tau[s]);
+  }
+  sp.G = (float)params->G;
+  for (int d = 0; d < 3; ++d) sp.F[d] = (float)params->F_ext[d];
+  memset(&sp.res, 0, sizeof sp.res);
+  c->t = 0;
+  c->rho_at = -1;
+  c->have_geometry = false;
+  c->have_state = false;
+  *out = c;
+  return LBM_OK;
+}
+
+void lbm_destroy(lbm_ctx *ctx) { delete ctx; }
+
+lbm_status lbm_set_geometry(lbm_ctx *c, const float *ns, const float *gads2) {
+  if (!c) return LBM_EINVAL;
+  if (!ns) return fail(c, LBM_EINVAL, "ns is NULL");
+  for (long long n = 0; n < c->N; ++n)
+    if (!(ns[n] >= 0.0f && ns[n] <= 1.0f))
+      return fail(c, LBM_EINVAL, "ns[%lld] = %g is outside [0, 1]", n, (double)ns[n]);
+  if (gads2)
+    for (long long n = 0; n < c->N; ++n)
+      if (!std::isfinite(gads2[n]))
+        return fail(c, LBM_EINVAL, "gads2[%lld] is not finite", n);
+  lbm_status st = upload(c, c->ws.ns, ns, (size_t)c->N);
+  if (st) return st;
+  if (gads2) {
+    st = upload(c, c->ws.stage, gads2, (size_t)c->N);
+    if (st) return st;
+  } else {
+    cudaError_t e = cudaMemsetAsync(c->ws.stage, 0, sizeof(float) * c->N, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "memset");
+  }
+  cudaError_t e = hmcsc::launch_adhesion_source(c->sp, c->ws, c->ws.stage, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "adhesion source kernel");
+  st = sync_stream(c, "set_geometry");
+  if (st) return st;
+  c->have_geometry = true;
+  c->rho_at = -1;
+  return LBM_OK;
+}
+
+lbm_status lbm_init_equilibrium(lbm_ctx *c, const float *rho_a,
+                                const float *rho_b) {
+  if (!c) return LBM_EINVAL;
+  if (!rho_a || !rho_b) return fail(c, LBM_EINVAL, "density array is NULL");
+  for (long long n = 0; n < c->N; ++n)
+    if (!(rho_a[n] > 0.0f) || !(rho_b[n] > 0.0f) || !std::isfinite(rho_a[n]) ||
+        !std::isfinite(rho_b[n]))
+      return fail(c, LBM_EINVAL, "densities at node %lld must be finite and > 0", n);
+  const size_t np = padded_stride(c);
+  lbm_status st = upload(c, c->ws.stage, rho_a, (size_t)c->N);
+  if (st) return st;
+  st = upload(c, c->ws.stage + np, rho_b, (size_t)c->N);
+  if (st) return st;
+  cudaError_t e = hmcsc::launch_init_equilibrium(c->sp, c->ws, c->ws.stage,
+                                                 c->ws.stage + np, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "init kernel");
+  st = sync_stream(c, "init_equilibrium");
+  if (st) return st;
+  c->t = 0;
+  c->rho_at = -1;
+  c->have_state = true;
+  return LBM_OK;
+}
+
+lbm_status lbm_set_populations(lbm_ctx *c, const float *f) {
+  if (!c) return LBM_EINVAL;
+  if (!f) return fail(c, LBM_EINVAL, "f is NULL");
+  const long long N = c->N;
+  for (int s = 0; s < 2; ++s)
+    for (long long n = 0; n < N; ++n) {
+      float r = 0.0f;
+      for (int i = 0; i < kQ; ++i) {
+        const float v = f[((size_t)s * kQ + i) * N + n];
+        if (!std::isfinite(v)) return fail(c, LBM_EINVAL, "population not finite");
+        r += v;
+      }
+      if (!(r > 0.0f)) return fail(c, LBM_EINVAL, "component %d density <= 0 at node %lld", s, n);
+    }
+  const size_t np = padded_stride(c);
+  for (int k = 0; k < 2 * kQ; ++k) {
+    cudaError_t e = cudaMemcpyAsync(c->ws.f + (size_t)k * np, f + (size_t)k * N,
+                                    sizeof(float) * N, cudaMemcpyHostToDevice, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "host-to-device copy");
+  }
+  lbm_status st = sync_stream(c, "set_populations");
+  if (st) return st;
+  c->t = 0;
+  c->rho_at = -1;
+  c->have_state = true;
+  return LBM_OK;
+}
+
+lbm_status lbm_get_populations(lbm_ctx *c, float *f) {
+  if (!c) return LBM_EINVAL;
+  if (!f) return fail(c, LBM_EINVAL, "f is NULL");
+  if (!c->have_state) return fail(c, LBM_ESTATE, "no state set");
+  const size_t np = padded_stride(c);
+  const long long N = c->N;
+  std::vector<float> raw((size_t)2 * kQ * np);
+  cudaError_t e = cudaMemcpyAsync(raw.data(), c->ws.f, raw.size() * sizeof(float),
+                                  cudaMemcpyDeviceToHost, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "device-to-host copy");
+  lbm_status st = sync_stream(c, "get_populations");
+  if (st) return st;
+  const int nx = c->params.nx, ny = c->params.ny, nz = c->params.nz;
+  for (int s = 0; s < 2; ++s)
+    for (int i = 0; i < kQ; ++i)
+      for (int z = 0; z < nz; ++z)
+        for (int y = 0; y < ny; ++y)
+          for (int x = 0; x < nx; ++x) {
+            const long long n = x + (long long)nx * (y + (long long)ny * z);
+            float v;
+            if (parity(c) == 0) {
+              v = raw[((size_t)s * kQ + i) * np + n];
+            } else {
+              // population i of node n sits in slot opp(i) of node n - c_i
+              const int xs = (x - hmcsc::cx(i) + nx) % nx;
+              const int ys = (y - hmcsc::cy(i) + ny) % ny;
+              const int zs = (z - hmcsc::cz(i) + nz) % nz;
+              const long long m = xs + (long long)nx * (ys + (long long)ny * zs);
+              v = raw[((size_t)s * kQ + hmcsc::opp(i)) * np + m];
+            }
+            f[((size_t)s * kQ + i) * N + n] = v;
+          }
+  return LBM_OK;
+}
+
+lbm_status lbm_set_bc(lbm_ctx *c, int face, int layers, double rho_a,
+                      double rho_b) {
+  if (!c) return LBM_EINVAL;
+  if (face < 0 || face >= kFaces) return fail(c, LBM_EINVAL, "face must be 0..5");
+  const int len = face < 2 ? c->params.nx : (face < 4 ? c->params.ny : c->params.nz);
+  if (layers < 0 || layers > len) return fail(c, LBM_EINVAL, "layers out of range");
+  if (layers > 0 && (!(rho_a > 0) || !(rho_b > 0) || !std::isfinite(rho_a) ||
+                     !std::isfinite(rho_b)))
+    return fail(c, LBM_EINVAL, "reservoir densities must be finite and > 0");
+  c->sp.res.layers[face] = layers;
+  c->sp.res.rho[face][0] = (float)rho_a;
+  c->sp.res.rho[face][1] = (float)rho_b;
+  int any = 0;
+  for (int k = 0; k < kFaces; ++k) any |= c->sp.res.layers[k] > 0;
+  c->sp.res.any = any;
+  return LBM_OK;
+}
+
+lbm_status lbm_density(lbm_ctx *c) {
+  if (!c) return LBM_EINVAL;
+  if (!c->have_geometry || !c->have_state)
+    return fail(c, LBM_ESTATE, "set geometry and state before stepping");
+  cudaError_t e = hmcsc::launch_density(c->sp, c->ws, parity(c), c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "density kernel");
+  c->rho_at = c->t;
+  return LBM_OK;
+}
+
+lbm_status lbm_collide_stream(lbm_ctx *c) {
+  if (!c) return LBM_EINVAL;
+  if (c->rho_at != c->t)
+    return fail(c, LBM_ESTATE, "lbm_density must precede lbm_collide_stream");
+  cudaError_t e = hmcsc::launch_collide_stream(c->sp, c->ws, parity(c), c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "collide/stream kernel");
+  c->t += 1;
+  return LBM_OK;
+}
+
+lbm_status lbm_step(lbm_ctx *c, int n_steps) {
+  if (!c) return LBM_EINVAL;
+  if (n_steps < 0) return fail(c, LBM_EINVAL, "n_steps < 0");
+  if (n_steps == 0) return LBM_OK;
+  if (!c->have_geometry || !c->have_state)
+    return fail(c, LBM_ESTATE, "set geometry and state before stepping");
+  for (int k = 0; k < n_steps; ++k) {
+    lbm_status st = lbm_density(c);
+    if (st) return st;
+    st = lbm_collide_stream(c);
+    if (st) return st;
+  }
+  return LBM_OK;
+}
+
+int64_t lbm_time(const lbm_ctx *c) { return c ? c->t : -1; }
+
+lbm_status lbm_read_fields(lbm_ctx *c, float *rho_a, float *rho_b, float *u,
+                           float *p) {
+  if (!c) return LBM_EINVAL;
+  if (!c->have_geometry || !c->have_state)
+    return fail(c, LBM_ESTATE, "no state set");
+  cudaError_t e = hmcsc::launch_density(c->sp, c->ws, parity(c), c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "density kernel");
+  c->rho_at = c->t;
+  e = hmcsc::launch_fields(c->sp, c->ws, parity(c), c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "fields kernel");
+  const size_t np = padded_stride(c);
+  const size_t bytes = sizeof(float) * (size_t)c->N;
+  float *dst[6] = {rho_a, rho_b, u, u ? u + c->N : nullptr,
+                   u ? u + 2 * c->N : nullptr, p};
+  for (int k = 0; k < 6; ++k) {
+    if (!dst[k]) continue;
+    e = cudaMemcpyAsync(dst[k], c->ws.stage + (size_t)k * np, bytes,
+                        cudaMemcpyDeviceToHost, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "device-to-host copy");
+  }
+  return sync_stream(c, "read_fields");
+}
+
+lbm_status lbm_reduce(lbm_ctx *c, lbm_observables *out) {
+  if (!c) return LBM_EINVAL;
+  if (!out) return fail(c, LBM_EINVAL, "out is NULL");
+  if (!c->have_geometry || !c->have_state)
+    return fail(c, LBM_ESTATE, "no state set");
+  cudaError_t e = hmcsc::launch_density(c->sp, c->ws, parity(c), c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "density kernel");
+  c->rho_at = c->t;
+  e = hmcsc::launch_reduce(c->sp, c->ws, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "reduce kernel");
+  double r[kRedK];
+  e = cudaMemcpyAsync(r, c->ws.red + (size_t)kRedBlocks * kRedK, sizeof r,
+                      cudaMemcpyDeviceToHost, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "device-to-host copy");
+  lbm_status st = sync_stream(c, "reduce");
+  if (st) return st;
+  out->mass[0] = r[0];
+  out->mass[1] = r[1];
+  out->sat1 = r[3] > 0.0 ? r[2] / r[3] : NAN;
+  const long long ext[3] = {c->params.nx, c->params.ny, c->params.nz};
+  for (int k = 0; k < kFaces; ++k) {
+    const int L = c->sp.res.layers[k];
+    if (L == 0) {
+      out->p_face[k] = NAN;
+      continue;
+    }
+    const int axis = k / 2;
+    const long long cnt = (long long)L * (ext[0] * ext[1] * ext[2] / ext[axis]);
+    out->p_face[k] = r[4 + k] / (double)cnt;
+  }
+  out->nonfinite = (int64_t)r[10];
+  if (out->nonfinite > 0)
+    return fail(c, LBM_ENAN, "%lld nodes have non-finite densities",
+                (long long)out->nonfinite);
+  return LBM_OK;
+}
+
+lbm_status lbm_sync(lbm_ctx *c, double timeout_s) {
+  if (!c) return LBM_EINVAL;
+  cudaEvent_t ev;
+  cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+  if (e != cudaSuccess) return cuda_fail(c, e, "event create");
+  e = cudaEventRecord(ev, c->stream);
+  if (e != cudaSuccess) {
+    cudaEventDestroy(ev);
+    return cuda_fail(c, e, "event record");
+  }
+  const auto t0 = std::chrono::steady_clock::now();
+  lbm_status st = LBM_OK;
+  for (;;) {
+    e = cudaEventQuery(ev);
+    if (e == cudaSuccess) break;
+    if (e != cudaErrorNotReady) {
+      st = cuda_fail(c, e, "stream");
+      break;
+    }
+    const double el = std::chrono::duration<double>(
+                          std::chrono::steady_clock::now() - t0).count();
+    if (el > timeout_s) {
+      st = fail(c, LBM_ETIMEOUT, "stream not finished after %.3f s", timeout_s);
+      break;
+    }
+    std::this_thread::sleep_for(std::chrono::microseconds(200));
+  }
+  cudaEventDestroy(ev);
+  return st;
+}
+
+size_t lbm_checkpoint_bytes(const lbm_ctx *c) {
+  if (!c) return 0;
+  return sizeof(CkptHeader) + sizeof(float) * 2 * kQ * (size_t)c->sp.np;
+}
+
+lbm_status lbm_save(lbm_ctx *c, void *host_buf, size_t bytes) {
+  if (!c) return LBM_EINVAL;
+  if (!host_buf || bytes < lbm_checkpoint_bytes(c))
+    return fail(c, LBM_EINVAL, "checkpoint buffer too small");
+  if (!c->have_state) return fail(c, LBM_ESTATE, "no state set");
+  CkptHeader h;
+  memset(&h, 0, sizeof h);
+  memcpy(h.magic, kMagic, 8);
+  h.version = 1;
+  h.storage = c->params.storage;
+  h.nx = c->params.nx;
+  h.ny = c->params.ny;
+  h.nz = c->params.nz;
+  h.t = c->t;
+  h.np = c->sp.np;
+  memcpy(host_buf, &h, sizeof h);
+  cudaError_t e = cudaMemcpyAsync((char *)host_buf + sizeof h, c->ws.f,
+                                  sizeof(float) * 2 * kQ * (size_t)c->sp.np,
+                                  cudaMemcpyDeviceToHost, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "device-to-host copy");
+  return sync_stream(c, "save");
+}
+
+lbm_status lbm_load(lbm_ctx *c, const void *host_buf, size_t bytes) {
+  if (!c) return LBM_EINVAL;
+  if (!host_buf || bytes < sizeof(CkptHeader))
+    return fail(c, LBM_EINVAL, "checkpoint buffer too small");
+  CkptHeader h;
+  memcpy(&h, host_buf, sizeof h);
+  if (memcmp(h.magic, kMagic, 8) != 0 || h.version != 1)
+    return fail(c, LBM_EINVAL, "not a checkpoint of this library");
+  if (h.nx != c->params.nx || h.ny != c->params.ny || h.nz != c->params.nz ||
+      h.storage != c->params.storage || h.np != c->sp.np || h.t < 0)
+    return fail(c, LBM_EINVAL, "checkpoint lattice or storage differs");
+  if (bytes < lbm_checkpoint_bytes(c))
+    return fail(c, LBM_EINVAL, "checkpoint truncated");
+  cudaError_t e = cudaMemcpyAsync(c->ws.f, (const char *)host_buf + sizeof h,
+                                  sizeof(float) * 2 * kQ * (size_t)c->sp.np,
+                                  cudaMemcpyHostToDevice, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "host-to-device copy");
+  lbm_status st = sync_stream(c, "load");
+  if (st) return st;
+  c->t = h.t;
+  c->rho_at = -1;
+  c->have_state = true;
+  return LBM_OK;
+}
+
+const char *lbm_last_error(const lbm_ctx *c) {
+  return c ? c->err.c_str() : "context is NULL";
+}
+
+}  // extern "C"

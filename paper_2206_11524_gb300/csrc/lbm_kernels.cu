@@ -1,0 +1,479 @@
+// lbm_kernels.cu -- sm_103a kernels of the HMCSC D3Q19 step.
+//
+// One time step is two launches:
+//   k_density        rho_sigma(x) = sum_i f_i,sigma(x)                (Eq. A.4)
+//   k_collide_stream moments, Shan-Chen forces (Eqs. 3-5), equilibrium
+//                    velocity (Eq. 6), equilibrium (Eq. A.3), gray collision
+//                    with partial bounce-back (Eq. 1), in-place streaming and
+//                    the density reservoirs (Sec. 4)
+// Populations live in one buffer per component in structure-of-arrays form
+// f[sigma][i][n] and stream in place with the AA pattern:
+//   even t: node n reads slot i at n, writes its post-collision f_i to slot
+//           opp(i) at n (population i of node n + c_i at t + 1);
+//   odd t:  node n reads population i from slot opp(i) at n - c_i, writes
+//           its post-collision f_i to slot i at n + c_i.
+// Every (slot, node) a thread writes is one it read itself, so the update is
+// race-free in place, and after an odd step the layout is natural again.
+#include "lbm_internal.cuh"
+
+namespace hmcsc {
+namespace {
+
+constexpr int kBX = 32, kBY = 4, kBZ = 2;
+
+// Periodic neighbourhood of one node: wrapped coordinates and offsets.
+struct Nbr {
+  int xw[3], yw[3], zw[3];
+  int row[3];  // yw * nx
+  int pln[3];  // zw * nx * ny
+  __device__ __forceinline__ int at(int dx, int dy, int dz) const {
+    return xw[dx + 1] + row[dy + 1] + pln[dz + 1];
+  }
+};
+
+__device__ __forceinline__ Nbr make_nbr(const StepParams &p, int x, int y,
+                                        int z) {
+  Nbr b;
+  b.xw[0] = x == 0 ? p.nx - 1 : x - 1;
+  b.xw[1] = x;
+  b.xw[2] = x == p.nx - 1 ? 0 : x + 1;
+  b.yw[0] = y == 0 ? p.ny - 1 : y - 1;
+  b.yw[1] = y;
+  b.yw[2] = y == p.ny - 1 ? 0 : y + 1;
+  b.zw[0] = z == 0 ? p.nz - 1 : z - 1;
+  b.zw[1] = z;
+  b.zw[2] = z == p.nz - 1 ? 0 : z + 1;
+  const int nxy = p.nx * p.ny;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    b.row[k] = b.yw[k] * p.nx;
+    b.pln[k] = b.zw[k] * nxy;
+  }
+  return b;
+}
+
+__device__ __forceinline__ const float *slot(const float *f, long long np,
+                                             int s, int i) {
+  return f + (size_t)(s * kQ + i) * (size_t)np;
+}
+__device__ __forceinline__ float *slot(float *f, long long np, int s, int i) {
+  return f + (size_t)(s * kQ + i) * (size_t)np;
+}
+
+// The 19 populations of component s at node n at the current time step.
+template <int PARITY>
+__device__ __forceinline__ void load_pops(const float *__restrict__ f,
+                                          long long np, const Nbr &nb, int n,
+                                          int s, float (&v)[kQ]) {
+#pragma unroll
+  for (int i = 0; i < kQ; ++i) {
+    if (PARITY == 0)
+      v[i] = slot(f, np, s, i)[n];
+    else
+      v[i] = slot(f, np, s, opp(i))[nb.at(-cx(i), -cy(i), -cz(i))];
+  }
+}
+
+// Zeroth moment, summed in direction order; k_density and k_collide_stream
+// share this order so both see bit-identical densities.
+__device__ __forceinline__ float sum19(const float (&v)[kQ]) {
+  float r = v[0];
+#pragma unroll
+  for (int i = 1; i < kQ; ++i) r += v[i];
+  return r;
+}
+
+__device__ __forceinline__ void first_moment(const float (&v)[kQ],
+                                             float (&j)[3]) {
+  j[0] = j[1] = j[2] = 0.0f;
+#pragma unroll
+  for (int i = 1; i < kQ; ++i) {
+    if (cx(i)) j[0] += cx(i) > 0 ? v[i] : -v[i];
+    if (cy(i)) j[1] += cy(i) > 0 ? v[i] : -v[i];
+    if (cz(i)) j[2] += cz(i) > 0 ? v[i] : -v[i];
+  }
+}
+
+// Total force per unit mass of each component, F_tot,sigma / rho_sigma
+// (Eqs. 3-5; rho_sigma cancels against the prefactor of Eqs. 3-4 and the
+// density ratio of Eq. 5, so no division by a vanishing component density):
+//   g_1 = -G S_2 + A + F_ext / rho,   g_2 = -G S_1 - A + F_ext / rho
+// with S_sigma = sum_i w_i rho_sigma(x + c_i) c_i and A = sum_i w_i a(x + c_i)
+// c_i, a = G_ads,2 n_s (G_ads,1 = -G_ads,2, Table 1).  Opposite directions
+// are summed as pairs, so a uniform field gives exactly zero.
+__device__ __forceinline__ void force_per_mass(const StepParams &p,
+                                               const float2 *__restrict__ rho,
+                                               const float *__restrict__ ads,
+                                               const Nbr &nb, float rho_tot,
+                                               float (&g1)[3], float (&g2)[3]) {
+  float s1[3] = {0.f, 0.f, 0.f}, s2[3] = {0.f, 0.f, 0.f}, sa[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+  for (int i = 1; i <= 9; ++i) {
+    const int mp = nb.at(cx(i), cy(i), cz(i));
+    const int mm = nb.at(-cx(i), -cy(i), -cz(i));
+    const float2 rp = __ldg(&rho[mp]);
+    const float2 rm = __ldg(&rho[mm]);
+    const float ap = __ldg(&ads[mp]);
+    const float am = __ldg(&ads[mm]);
+    const float d1 = wgt(i) * (rp.x - rm.x);
+    const float d2 = wgt(i) * (rp.y - rm.y);
+    const float da = wgt(i) * (ap - am);
+    if (cx(i)) { s1[0] += cx(i) > 0 ? d1 : -d1; s2[0] += cx(i) > 0 ? d2 : -d2; sa[0] += cx(i) > 0 ? da : -da; }
+    if (cy(i)) { s1[1] += cy(i) > 0 ? d1 : -d1; s2[1] += cy(i) > 0 ? d2 : -d2; sa[1] += cy(i) > 0 ? da : -da; }
+    if (cz(i)) { s1[2] += cz(i) > 0 ? d1 : -d1; s2[2] += cz(i) > 0 ? d2 : -d2; sa[2] += cz(i) > 0 ? da : -da; }
+  }
+  const float inv_rho = 1.0f / rho_tot;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const float fe = p.F[d] * inv_rho;
+    g1[d] = -p.G * s2[d] + sa[d] + fe;
+    g2[d] = -p.G * s1[d] - sa[d] + fe;
+  }
+}
+
+// Reservoir face holding node (x, y, z), -1 if none; the higher face wins.
+__device__ __forceinline__ int res_face(const StepParams &p, int x, int y,
+                                        int z) {
+  const int *L = p.res.layers;
+  int face = -1;
+  if (L[0] && x < L[0]) face = 0;
+  if (L[1] && x >= p.nx - L[1]) face = 1;
+  if (L[2] && y < L[2]) face = 2;
+  if (L[3] && y >= p.ny - L[3]) face = 3;
+  if (L[4] && z < L[4]) face = 4;
+  if (L[5] && z >= p.nz - L[5]) face = 5;
+  return face;
+}
+
+// True when some neighbour x + c_i (periodic) may lie in a reservoir.
+__device__ __forceinline__ bool near_reservoir(const StepParams &p, int x,
+                                               int y, int z) {
+  const int *L = p.res.layers;
+  bool nx_ = (L[0] && (x <= L[0] || x == p.nx - 1)) ||
+             (L[1] && (x >= p.nx - 1 - L[1] || x == 0));
+  bool ny_ = (L[2] && (y <= L[2] || y == p.ny - 1)) ||
+             (L[3] && (y >= p.ny - 1 - L[3] || y == 0));
+  bool nz_ = (L[4] && (z <= L[4] || z == p.nz - 1)) ||
+             (L[5] && (z >= p.nz - 1 - L[5] || z == 0));
+  return nx_ || ny_ || nz_;
+}
+
+// Store the post-collision population i of component s of node n; it becomes
+// population i of node n + c_i at t + 1.  If that node is in a reservoir, the
+// prescribed equilibrium w_i rho_res at rest is stored instead (the reset of
+// Sec. 4, applied as the population arrives).
+template <int PARITY>
+__device__ __forceinline__ void put(float *__restrict__ f, const StepParams &p,
+                                   const Nbr &nb, int n, int s, int i,
+                                   float val, bool near) {
+  if (near) {
+    const int face = res_face(p, nb.xw[cx(i) + 1], nb.yw[cy(i) + 1],
+                              nb.zw[cz(i) + 1]);
+    if (face >= 0) val = wgt(i) * p.res.rho[face][s];
+  }
+  if (PARITY == 0)
+    slot(f, p.np, s, opp(i))[n] = val;
+  else
+    slot(f, p.np, s, i)[nb.at(cx(i), cy(i), cz(i))] = val;
+}
+
+// Eq. 1 for one component: (1 - n_s)[f_i - (f_i - f^eq_i)/tau] + n_s f_opp(i)
+// with f^eq of Eq. A.3 at (rho_s, u), computed for opposite pairs at once.
+// The rest population's equilibrium is taken as rho_s minus the other 18
+// (sum_i f^eq_i = rho_s holds exactly for Eq. A.3 on D3Q19), which keeps the
+// rounding of the float weights from leaking mass step after step.
+template <int PARITY>
+__device__ __forceinline__ void collide_put(float *__restrict__ f,
+                                            const StepParams &p, const Nbr &nb,
+                                            int n, int s, const float (&v)[kQ],
+                                            float rho_s, const float (&u)[3],
+                                            float nsx, bool near) {
+  const float om = p.omega[s];
+  const float a = (1.0f - nsx) * (1.0f - om);
+  const float b = (1.0f - nsx) * om;
+  const float usq = 1.5f * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+  float moving = 0.0f;
+#pragma unroll
+  for (int i = 1; i <= 9; ++i) {
+    const int j = i + 9;
+    const float cu = cx(i) * u[0] + cy(i) * u[1] + cz(i) * u[2];
+    const float wr = wgt(i) * rho_s;
+    const float even = wr * (1.0f + 4.5f * cu * cu - usq);
+    const float odd = wr * 3.0f * cu;
+    const float fe_i = even + odd, fe_j = even - odd;
+    moving += fe_i + fe_j;
+    put<PARITY>(f, p, nb, n, s, i, a * v[i] + b * fe_i + nsx * v[j], near);
+    put<PARITY>(f, p, nb, n, s, j, a * v[j] + b * fe_j + nsx * v[i], near);
+  }
+  const float fe_0 = rho_s - moving;
+  put<PARITY>(f, p, nb, n, s, 0, a * v[0] + b * fe_0 + nsx * v[0], near);
+}
+
+template <int PARITY>
+__global__ void __launch_bounds__(kBX * kBY * kBZ)
+    k_density(StepParams p, Workspace w) {
+  const int x = blockIdx.x * kBX + threadIdx.x;
+  const int y = blockIdx.y * kBY + threadIdx.y;
+  const int z = blockIdx.z * kBZ + threadIdx.z;
+  if (x >= p.nx || y >= p.ny || z >= p.nz) return;
+  const Nbr nb = make_nbr(p, x, y, z);
+  const int n = nb.at(0, 0, 0);
+  float v[kQ];
+  load_pops<PARITY>(w.f, p.np, nb, n, 0, v);
+  const float r1 = sum19(v);
+  load_pops<PARITY>(w.f, p.np, nb, n, 1, v);
+  const float r2 = sum19(v);
+  w.rho[n] = make_float2(r1, r2);
+}
+
+template <int PARITY>
+__global__ void __launch_bounds__(kBX * kBY * kBZ)
+    k_collide_stream(StepParams p, Workspace w) {
+  const int x = blockIdx.x * kBX + threadIdx.x;
+  const int y = blockIdx.y * kBY + threadIdx.y;
+  const int z = blockIdx.z * kBZ + threadIdx.z;
+  if (x >= p.nx || y >= p.ny || z >= p.nz) return;
+  const Nbr nb = make_nbr(p, x, y, z);
+  const int n = nb.at(0, 0, 0);
+
+  float f1[kQ], f2[kQ];
+  load_pops<PARITY>(w.f, p.np, nb, n, 0, f1);
+  load_pops<PARITY>(w.f, p.np, nb, n, 1, f2);
+  const float r1 = sum19(f1), r2 = sum19(f2);
+  float j1[3], j2[3];
+  first_moment(f1, j1);
+  first_moment(f2, j2);
+
+  float g1[3], g2[3];
+  force_per_mass(p, w.rho, w.ads, nb, r1 + r2, g1, g2);
+
+  // Eq. 6: common velocity sum_s j_s/tau_s / sum_s rho_s/tau_s, then the
+  // Shan-Chen shift tau_s F_tot,s / rho_s = tau_s g_s.
+  const float inv_den = 1.0f / (r1 * p.omega[0] + r2 * p.omega[1]);
+  float u1[3], u2[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const float uc = (j1[d] * p.omega[0] + j2[d] * p.omega[1]) * inv_den;
+    u1[d] = uc + p.tau[0] * g1[d];
+    u2[d] = uc + p.tau[1] * g2[d];
+  }
+
+  const float nsx = w.ns[n];
+  const bool near = p.res.any && near_reservoir(p, x, y, z);
+  collide_put<PARITY>(w.f, p, nb, n, 0, f1, r1, u1, nsx, near);
+  collide_put<PARITY>(w.f, p, nb, n, 1, f2, r2, u2, nsx, near);
+}
+
+// Macroscopic fields of the current state into the staging planes:
+// rho_1, rho_2, u_macro (Eq. 7) x, y, z, p (Eq. A.6).
+template <int PARITY>
+__global__ void __launch_bounds__(kBX * kBY * kBZ)
+    k_fields(StepParams p, Workspace w) {
+  const int x = blockIdx.x * kBX + threadIdx.x;
+  const int y = blockIdx.y * kBY + threadIdx.y;
+  const int z = blockIdx.z * kBZ + threadIdx.z;
+  if (x >= p.nx || y >= p.ny || z >= p.nz) return;
+  const Nbr nb = make_nbr(p, x, y, z);
+  const int n = nb.at(0, 0, 0);
+  float f1[kQ], f2[kQ];
+  load_pops<PARITY>(w.f, p.np, nb, n, 0, f1);
+  load_pops<PARITY>(w.f, p.np, nb, n, 1, f2);
+  const float r1 = sum19(f1), r2 = sum19(f2);
+  float j1[3], j2[3];
+  first_moment(f1, j1);
+  first_moment(f2, j2);
+  float g1[3], g2[3];
+  const float rho = r1 + r2;
+  force_per_mass(p, w.rho, w.ads, nb, rho, g1, g2);
+  const float fluid = 1.0f - w.ns[n];
+  const long long np = p.np;
+  w.stage[n] = r1;
+  w.stage[np + n] = r2;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const float m = (j1[d] + 0.5f * r1 * g1[d]) + (j2[d] + 0.5f * r2 * g2[d]);
+    w.stage[(2 + d) * np + n] = fluid * m / rho;
+  }
+  w.stage[5 * np + n] = (rho + p.G * r1 * r2) * (1.0f / 3.0f);
+}
+
+__global__ void k_init_equilibrium(StepParams p, Workspace w,
+                                   const float *__restrict__ rho1,
+                                   const float *__restrict__ rho2) {
+  const long long N = (long long)p.nx * p.ny * p.nz;
+  for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
+       n += (long long)gridDim.x * blockDim.x) {
+    const float r1 = rho1[n], r2 = rho2[n];
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) {
+      slot(w.f, p.np, 0, i)[n] = wgt(i) * r1;
+      slot(w.f, p.np, 1, i)[n] = wgt(i) * r2;
+    }
+  }
+}
+
+__global__ void k_adhesion_source(StepParams p, Workspace w,
+                                  const float *__restrict__ gads2) {
+  const long long N = (long long)p.nx * p.ny * p.nz;
+  for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
+       n += (long long)gridDim.x * blockDim.x)
+    w.ads[n] = gads2[n] * w.ns[n];
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block partial sums of the observables (fixed grid, fixed order).
+__global__ void __launch_bounds__(kRedThreads) k_reduce(StepParams p,
+                                                        Workspace w) {
+  double acc[kRedK];
+#pragma unroll
+  for (int k = 0; k < kRedK; ++k) acc[k] = 0.0;
+  const long long N = (long long)p.nx * p.ny * p.nz;
+  const int *L = p.res.layers;
+  for (long long n = blockIdx.x * (long long)kRedThreads + threadIdx.x; n < N;
+       n += (long long)kRedBlocks * kRedThreads) {
+    const int x = (int)(n % p.nx);
+    const int y = (int)((n / p.nx) % p.ny);
+    const int z = (int)(n / ((long long)p.nx * p.ny));
+    const float2 r = w.rho[n];
+    acc[0] += r.x;
+    acc[1] += r.y;
+    if (!isfinite(r.x) || !isfinite(r.y)) acc[10] += 1.0;
+    const bool in[kFaces] = {L[0] && x < L[0], L[1] && x >= p.nx - L[1],
+                             L[2] && y < L[2], L[3] && y >= p.ny - L[3],
+                             L[4] && z < L[4], L[5] && z >= p.nz - L[5]};
+    bool any = false;
+    const double pr =
+        ((double)r.x + (double)r.y + (double)p.G * (double)r.x * (double)r.y) / 3.0;
+#pragma unroll
+    for (int k = 0; k < kFaces; ++k)
+      if (in[k]) {
+        any = true;
+        acc[4 + k] += pr;
+      }
+    if (!any) {
+      const double wgt_fluid = 1.0 - (double)w.ns[n];
+      acc[3] += wgt_fluid;
+      if (r.x >= 0.5f) acc[2] += wgt_fluid;
+    }
+  }
+  __shared__ double sm[kRedThreads / 32][kRedK];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < kRedK; ++k) {
+    const double v = warp_sum(acc[k]);
+    if (lane == 0) sm[warp][k] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < kRedK) {
+    double t = 0.0;
+    for (int wi = 0; wi < kRedThreads / 32; ++wi) t += sm[wi][threadIdx.x];
+    w.red[blockIdx.x * kRedK + threadIdx.x] = t;
+  }
+}
+
+__global__ void k_reduce_final(Workspace w) {
+  const int k = threadIdx.x;
+  if (k >= kRedK) return;
+  double t = 0.0;
+  for (int b = 0; b < kRedBlocks; ++b) t += w.red[b * kRedK + k];
+  w.red[kRedBlocks * kRedK + k] = t;
+}
+
+dim3 node_grid(const StepParams &p) {
+  return dim3((p.nx + kBX - 1) / kBX, (p.ny + kBY - 1) / kBY,
+              (p.nz + kBZ - 1) / kBZ);
+}
+
+int flat_blocks(const StepParams &p) {
+  long long N = (long long)p.nx * p.ny * p.nz;
+  long long b = (N + 255) / 256;
+  return (int)(b < 4864 ? (b < 1 ? 1 : b) : 4864);
+}
+
+}  // namespace
+
+size_t workspace_bytes(long long nx, long long ny, long long nz, Workspace *out,
+                       char *base) {
+  const long long N = nx * ny * nz;
+  const long long np = (N + 63) / 64 * 64;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t at = off;
+    off += (bytes + 255) / 256 * 256;
+    return at;
+  };
+  size_t o_f = take(sizeof(float) * 2 * kQ * (size_t)np);
+  size_t o_rho = take(sizeof(float2) * (size_t)np);
+  size_t o_ns = take(sizeof(float) * (size_t)np);
+  size_t o_ads = take(sizeof(float) * (size_t)np);
+  size_t o_stage = take(sizeof(float) * 6 * (size_t)np);
+  size_t o_red = take(sizeof(double) * (kRedBlocks + 1) * kRedK);
+  if (out) {
+    out->f = (float *)(base + o_f);
+    out->rho = (float2 *)(base + o_rho);
+    out->ns = (float *)(base + o_ns);
+    out->ads = (float *)(base + o_ads);
+    out->stage = (float *)(base + o_stage);
+    out->red = (double *)(base + o_red);
+  }
+  return off;
+}
+
+cudaError_t launch_init_equilibrium(const StepParams &p, const Workspace &w,
+                                    const float *rho_a, const float *rho_b,
+                                    cudaStream_t s) {
+  k_init_equilibrium<<<flat_blocks(p), 256, 0, s>>>(p, w, rho_a, rho_b);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adhesion_source(const StepParams &p, const Workspace &w,
+                                   const float *gads2, cudaStream_t s) {
+  k_adhesion_source<<<flat_blocks(p), 256, 0, s>>>(p, w, gads2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_density(const StepParams &p, const Workspace &w, int parity,
+                           cudaStream_t s) {
+  const dim3 block(kBX, kBY, kBZ);
+  if (parity == 0)
+    k_density<0><<<node_grid(p), block, 0, s>>>(p, w);
+  else
+    k_density<1><<<node_grid(p), block, 0, s>>>(p, w);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_collide_stream(const StepParams &p, const Workspace &w,
+                                  int parity, cudaStream_t s) {
+  const dim3 block(kBX, kBY, kBZ);
+  if (parity == 0)
+    k_collide_stream<0><<<node_grid(p), block, 0, s>>>(p, w);
+  else
+    k_collide_stream<1><<<node_grid(p), block, 0, s>>>(p, w);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fields(const StepParams &p, const Workspace &w, int parity,
+                          cudaStream_t s) {
+  const dim3 block(kBX, kBY, kBZ);
+  if (parity == 0)
+    k_fields<0><<<node_grid(p), block, 0, s>>>(p, w);
+  else
+    k_fields<1><<<node_grid(p), block, 0, s>>>(p, w);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reduce(const StepParams &p, const Workspace &w,
+                          cudaStream_t s) {
+  k_reduce<<<kRedBlocks, kRedThreads, 0, s>>>(p, w);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_reduce_final<<<1, 32, 0, s>>>(w);
+  return cudaGetLastError();
+}
+
+}  // namespace hmcsc

@@ -1,0 +1,312 @@
+"""ctypes binding of the C ABI in ``include/lbm.h`` (argument marshalling only).
+
+The functions here carry the C names (``lbm_create``, ``lbm_step`` ...) and
+take the same arguments; every step of the computation runs in the CUDA
+library.  ``Lattice`` is a thin convenience wrapper that allocates the device
+workspace as a PyTorch tensor and passes PyTorch's current stream.
+
+If the compiled library is missing the import fails loudly: there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_ENAN, LBM_ETIMEOUT, \
+    LBM_ESTATE, LBM_EINTERNAL = range(8)
+LBM_STORAGE_F32 = 0
+STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENAN",
+                5: "ETIMEOUT", 6: "ESTATE", 7: "EINTERNAL"}
+
+#: every entry point declared in include/lbm.h
+ABI_SYMBOLS = (
+    "lbm_workspace_bytes", "lbm_create", "lbm_destroy", "lbm_set_geometry",
+    "lbm_init_equilibrium", "lbm_set_populations", "lbm_get_populations",
+    "lbm_set_bc", "lbm_step", "lbm_density", "lbm_collide_stream", "lbm_time",
+    "lbm_read_fields", "lbm_reduce", "lbm_sync", "lbm_checkpoint_bytes",
+    "lbm_save", "lbm_load", "lbm_last_error",
+)
+
+
+class lbm_params(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
+                ("nz", ctypes.c_int32), ("storage", ctypes.c_int32),
+                ("tau", ctypes.c_double * 2), ("G", ctypes.c_double),
+                ("F_ext", ctypes.c_double * 3)]
+
+
+class lbm_observables(ctypes.Structure):
+    _fields_ = [("mass", ctypes.c_double * 2), ("sat1", ctypes.c_double),
+                ("p_face", ctypes.c_double * 6), ("nonfinite", ctypes.c_int64)]
+
+
+class LbmError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+_LIBPATH = _build.LIB
+
+
+def library_path() -> str:
+    return _LIBPATH
+
+
+def load(path: str | None = None):
+    """Load the shared library (build it first with ``build.build()``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or _LIBPATH
+    if not os.path.exists(path):
+        raise ImportError(
+            f"CUDA library not built: {path} is missing "
+            "(run __graft_entry__.build() or python -m paper_2206_11524_gb300.build)")
+    lib = ctypes.CDLL(path)
+    vp, fp, dp = ctypes.c_void_p, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_double)
+    P = ctypes.POINTER(lbm_params)
+    sig = {
+        "lbm_workspace_bytes": (ctypes.c_size_t, [P]),
+        "lbm_create": (ctypes.c_int, [P, vp, ctypes.c_size_t, vp, ctypes.POINTER(vp)]),
+        "lbm_destroy": (None, [vp]),
+        "lbm_set_geometry": (ctypes.c_int, [vp, fp, fp]),
+        "lbm_init_equilibrium": (ctypes.c_int, [vp, fp, fp]),
+        "lbm_set_populations": (ctypes.c_int, [vp, fp]),
+        "lbm_get_populations": (ctypes.c_int, [vp, fp]),
+        "lbm_set_bc": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double]),
+        "lbm_step": (ctypes.c_int, [vp, ctypes.c_int]),
+        "lbm_density": (ctypes.c_int, [vp]),
+        "lbm_collide_stream": (ctypes.c_int, [vp]),
+        "lbm_time": (ctypes.c_int64, [vp]),
+        "lbm_read_fields": (ctypes.c_int, [vp, fp, fp, fp, fp]),
+        "lbm_reduce": (ctypes.c_int, [vp, ctypes.POINTER(lbm_observables)]),
+        "lbm_sync": (ctypes.c_int, [vp, ctypes.c_double]),
+        "lbm_checkpoint_bytes": (ctypes.c_size_t, [vp]),
+        "lbm_save": (ctypes.c_int, [vp, vp, ctypes.c_size_t]),
+        "lbm_load": (ctypes.c_int, [vp, vp, ctypes.c_size_t]),
+        "lbm_last_error": (ctypes.c_char_p, [vp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _f32(a, n=None):
+    """Contiguous float32 host array and its pointer (or NULL)."""
+    if a is None:
+        return None, None
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    if n is not None and a.size != n:
+        raise ValueError(f"expected {n} values, got {a.size}")
+    return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
+# ---- thin wrappers with the C names ---------------------------------------
+
+def lbm_workspace_bytes(params: lbm_params) -> int:
+    return load().lbm_workspace_bytes(ctypes.byref(params))
+
+
+def lbm_create(params: lbm_params, d_workspace: int, workspace_bytes: int,
+               cuda_stream: int) -> ctypes.c_void_p:
+    ctx = ctypes.c_void_p()
+    st = load().lbm_create(ctypes.byref(params), ctypes.c_void_p(d_workspace),
+                           workspace_bytes, ctypes.c_void_p(cuda_stream),
+                           ctypes.byref(ctx))
+    if st != LBM_OK:
+        raise LbmError(st, "lbm_create failed")
+    return ctx
+
+
+def _check(ctx, st):
+    if st != LBM_OK:
+        msg = load().lbm_last_error(ctx)
+        raise LbmError(st, msg.decode() if msg else "")
+    return st
+
+
+def lbm_destroy(ctx):
+    load().lbm_destroy(ctx)
+
+
+def lbm_set_geometry(ctx, ns, gads2=None, n=None):
+    a, pa = _f32(ns, n)
+    b, pb = _f32(gads2, n)
+    return _check(ctx, load().lbm_set_geometry(ctx, pa, pb))
+
+
+def lbm_init_equilibrium(ctx, rho_a, rho_b, n=None):
+    a, pa = _f32(rho_a, n)
+    b, pb = _f32(rho_b, n)
+    return _check(ctx, load().lbm_init_equilibrium(ctx, pa, pb))
+
+
+def lbm_set_populations(ctx, f):
+    a, pa = _f32(f)
+    return _check(ctx, load().lbm_set_populations(ctx, pa))
+
+
+def lbm_get_populations(ctx, out: np.ndarray):
+    assert out.dtype == np.float32 and out.flags["C_CONTIGUOUS"]
+    return _check(ctx, load().lbm_get_populations(
+        ctx, out.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+
+
+def lbm_set_bc(ctx, face, layers, rho_a, rho_b):
+    return _check(ctx, load().lbm_set_bc(ctx, face, layers, rho_a, rho_b))
+
+
+def lbm_step(ctx, n_steps):
+    return _check(ctx, load().lbm_step(ctx, int(n_steps)))
+
+
+def lbm_density(ctx):
+    return _check(ctx, load().lbm_density(ctx))
+
+
+def lbm_collide_stream(ctx):
+    return _check(ctx, load().lbm_collide_stream(ctx))
+
+
+def lbm_time(ctx) -> int:
+    return load().lbm_time(ctx)
+
+
+def lbm_read_fields(ctx, rho_a=None, rho_b=None, u=None, p=None):
+    def ptr(a):
+        if a is None:
+            return None
+        assert a.dtype == np.float32 and a.flags["C_CONTIGUOUS"]
+        return a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+    return _check(ctx, load().lbm_read_fields(ctx, ptr(rho_a), ptr(rho_b),
+                                              ptr(u), ptr(p)))
+
+
+def lbm_reduce(ctx, allow_nan: bool = False) -> lbm_observables:
+    out = lbm_observables()
+    st = load().lbm_reduce(ctx, ctypes.byref(out))
+    if st == LBM_ENAN and allow_nan:
+        return out
+    _check(ctx, st)
+    return out
+
+
+def lbm_sync(ctx, timeout_s: float):
+    return _check(ctx, load().lbm_sync(ctx, float(timeout_s)))
+
+
+def lbm_checkpoint_bytes(ctx) -> int:
+    return load().lbm_checkpoint_bytes(ctx)
+
+
+def lbm_save(ctx, buf: bytearray):
+    cbuf = (ctypes.c_char * len(buf)).from_buffer(buf)
+    return _check(ctx, load().lbm_save(ctx, ctypes.addressof(cbuf), len(buf)))
+
+
+def lbm_load(ctx, buf: bytes):
+    cbuf = ctypes.create_string_buffer(bytes(buf), len(buf))
+    return _check(ctx, load().lbm_load(ctx, ctypes.addressof(cbuf), len(buf)))
+
+
+def lbm_last_error(ctx) -> str:
+    msg = load().lbm_last_error(ctx)
+    return msg.decode() if msg else ""
+
+
+# ---- convenience wrapper ------------------------------------------------
+
+class Lattice:
+    """One HMCSC lattice on the current CUDA device.
+
+    Allocates the device workspace with PyTorch (``torch.empty`` uint8) and
+    runs on PyTorch's current stream (or ``stream``).  Arrays in and out are
+    numpy, shaped ``[nz, ny, nx]`` (populations ``[2, 19, nz, ny, nx]``).
+    """
+
+    def __init__(self, nx, ny, nz, tau=(1.0, 1.0), G=1.75, F_ext=(0, 0, 0),
+                 stream=None, device=None):
+        import torch
+        self.shape = (nz, ny, nx)
+        self.N = nx * ny * nz
+        p = lbm_params()
+        p.nx, p.ny, p.nz, p.storage = nx, ny, nz, LBM_STORAGE_F32
+        p.tau[0], p.tau[1] = tau
+        p.G = G
+        for d in range(3):
+            p.F_ext[d] = F_ext[d]
+        self.params = p
+        nbytes = lbm_workspace_bytes(p)
+        if nbytes == 0:
+            raise LbmError(LBM_EINVAL, "invalid lattice parameters")
+        dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(dev)
+        self.ctx = lbm_create(p, self.workspace.data_ptr(), nbytes,
+                              self.stream.cuda_stream)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            lbm_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_geometry(self, ns, gads2=None):
+        lbm_set_geometry(self.ctx, ns, gads2, self.N)
+
+    def init_equilibrium(self, rho_a, rho_b):
+        lbm_init_equilibrium(self.ctx, rho_a, rho_b, self.N)
+
+    def set_populations(self, f):
+        lbm_set_populations(self.ctx, np.asarray(f).reshape(2, 19, self.N))
+
+    def populations(self):
+        out = np.empty((2, 19) + self.shape, dtype=np.float32)
+        lbm_get_populations(self.ctx, out)
+        return out
+
+    def set_bc(self, face, layers, rho_a=1.0, rho_b=1.0):
+        lbm_set_bc(self.ctx, face, layers, rho_a, rho_b)
+
+    def step(self, n=1):
+        lbm_step(self.ctx, n)
+
+    @property
+    def t(self):
+        return lbm_time(self.ctx)
+
+    def fields(self):
+        out = {"rho_a": np.empty(self.shape, np.float32),
+               "rho_b": np.empty(self.shape, np.float32),
+               "u": np.empty((3,) + self.shape, np.float32),
+               "p": np.empty(self.shape, np.float32)}
+        lbm_read_fields(self.ctx, out["rho_a"], out["rho_b"], out["u"], out["p"])
+        return out
+
+    def observables(self, allow_nan=False):
+        o = lbm_reduce(self.ctx, allow_nan)
+        return {"mass": np.array(o.mass[:]), "sat1": o.sat1,
+                "p_face": np.array(o.p_face[:]), "nonfinite": o.nonfinite}
+
+    def save(self) -> bytearray:
+        buf = bytearray(lbm_checkpoint_bytes(self.ctx))
+        lbm_save(self.ctx, buf)
+        return buf
+
+    def load(self, buf):
+        lbm_load(self.ctx, buf)

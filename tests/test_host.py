@@ -1,0 +1,97 @@
+"""CPU tests of the host side: the C library builds, loads and exports every
+entry point of include/lbm.h; argument validation that runs before any CUDA
+call; the paper's parameter conversions."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2206_11524_gb300 import build, lbm, params
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+GOLDEN = os.path.join(ROOT, "tests", "golden")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return lbm.load()
+
+
+def _header_symbols():
+    src = open(os.path.join(ROOT, "include", "lbm.h")).read()
+    return sorted(set(re.findall(r"^LBM_API\s+[\w\s\*]+?\b(lbm_\w+)\s*\(", src, re.M)))
+
+
+def test_header_declares_the_binding_symbols():
+    assert _header_symbols() == sorted(lbm.ABI_SYMBOLS)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in _header_symbols():
+        assert hasattr(lib, name), name
+    # nothing else of the library's internals leaks as a C symbol
+    out = os.popen(f"nm -D --defined-only {build.LIB}").read()
+    exported = {l.split()[-1] for l in out.splitlines() if " T " in l}
+    assert set(_header_symbols()) <= exported
+    assert not [s for s in exported if "hmcsc" in s]
+
+
+def _params(nx=8, ny=4, nz=2, tau=(1.0, 1.0)):
+    p = lbm.lbm_params()
+    p.nx, p.ny, p.nz, p.storage = nx, ny, nz, lbm.LBM_STORAGE_F32
+    p.tau[0], p.tau[1] = tau
+    p.G = 1.75
+    return p
+
+
+def test_workspace_bytes_and_validation(lib):
+    n = lbm.lbm_workspace_bytes(_params())
+    assert n >= 2 * 19 * 64 * 4 and n % 256 == 0
+    big = lbm.lbm_workspace_bytes(_params(256, 256, 256))
+    assert big >= 16777216 * (2 * 19 * 4 + 8 + 8)
+    assert lbm.lbm_workspace_bytes(_params(0, 4, 4)) == 0
+    assert lbm.lbm_workspace_bytes(_params(tau=(0.5, 1.0))) == 0
+    assert lbm.lbm_workspace_bytes(_params(70000, 70000, 1)) == 0  # > 2^31 nodes
+
+
+def test_create_rejects_bad_arguments_before_touching_the_gpu(lib):
+    p = _params()
+    ctx = ctypes.c_void_p()
+    st = lib.lbm_create(ctypes.byref(p), None, 1 << 20, None, ctypes.byref(ctx))
+    assert st == lbm.LBM_EINVAL
+    st = lib.lbm_create(ctypes.byref(p), ctypes.c_void_p(256), 16, None,
+                        ctypes.byref(ctx))
+    assert st == lbm.LBM_ENOMEM
+    st = lib.lbm_create(ctypes.byref(p), ctypes.c_void_p(257), 1 << 30, None,
+                        ctypes.byref(ctx))
+    assert st == lbm.LBM_EINVAL          # workspace not 256-byte aligned
+    assert lib.lbm_time(None) == -1
+    assert lib.lbm_last_error(None) == b"context is NULL"
+
+
+def _golden(name):
+    rows = []
+    for line in open(os.path.join(GOLDEN, name)):
+        line = line.split("#")[0].strip()
+        if line:
+            rows.append([float(v) for v in line.split()])
+    return np.array(rows)
+
+
+def test_contact_angle_conversion_matches_table3():
+    """Eq. 15 with Table 1's parameters reproduces the theta_H column of
+    Table 3 to its printed precision."""
+    for gads, theta in _golden("washburn_contact_angle_table3.txt"):
+        assert abs(params.contact_angle_from_gads(gads) - theta) < 0.051
+        back = params.gads_from_contact_angle(params.contact_angle_from_gads(gads))
+        assert abs(back - gads) < 1e-12
+
+
+def test_binder_wettability_and_viscosity():
+    # theta = 60 deg binder (Sec. 4): G_ads,2 = 1.75 * 0.98 / 8
+    assert abs(params.gads_from_contact_angle(60.0) - 0.214375) < 1e-12
+    assert abs(params.viscosity(1.0) - 1 / 6) < 1e-15       # Table 1: 1.667e-1
+    assert abs(params.permeability(0.5) - 1 / 12) < 1e-15   # Eq. 2
