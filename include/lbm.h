@@ -50,7 +50,8 @@ typedef enum {
   LBM_ENAN = 4,      /* a density became non-finite                     */
   LBM_ETIMEOUT = 5,  /* lbm_sync: the stream did not finish in time     */
   LBM_ESTATE = 6,    /* call out of order (e.g. step before geometry)   */
-  LBM_EINTERNAL = 7  /* a kernel reported an internal inconsistency     */
+  LBM_EINTERNAL = 7, /* a kernel reported an internal inconsistency    */
+  LBM_ETOOLARGE = 8  /* lattice beyond LBM_NOALLOC_MAX_NODES            */
 } lbm_status;
 
 typedef enum {
@@ -168,6 +169,42 @@ LBM_API lbm_status lbm_load(lbm_ctx *ctx, const void *host_buf, size_t bytes);
 
 /* Message of the last error on this context ("" if none). */
 LBM_API const char *lbm_last_error(const lbm_ctx *ctx);
+
+/* ---- Allocation-free observables -----------------------------------------
+ * The paper has no counterpart to this entry point: it exists for callers
+ * that cannot call cudaMalloc where they need the observables -- a host
+ * framework that only lends out its own fixed buffers, a real-time loop in
+ * which an allocation would stall the device, a plugin that never owns a
+ * workspace.  It computes what lbm_reduce computes (masses, S_1 of Eq. 19,
+ * reservoir mean pressures of Eq. A.6, non-finite count) from density fields
+ * the caller already holds on the device, and allocates nothing: its scratch
+ * is a fixed array of about 360 KB inside the library's device image, which
+ * every GPU that loads the library keeps until the process exits.
+ *
+ *   d_rho_a, d_rho_b, d_ns  device arrays [N] (float32, x fastest), read only
+ *   nx, ny, nz              lattice size, N = nx*ny*nz <= LBM_NOALLOC_MAX_NODES
+ *                           (larger lattices return LBM_ETOOLARGE, nothing run)
+ *   layers[6]               reservoir layers per face (-x,+x,-y,+y,-z,+z) as
+ *                           given to lbm_set_bc; NULL = no reservoirs
+ *   G                       G_inter,12 for the pressure of Eq. A.6
+ *   cuda_stream             stream to run on (NULL = legacy default stream)
+ *   out                     host result; waits for the stream
+ *
+ * The first call on each device looks up the scratch array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls share the one scratch array and it
+ * keeps the last call's contents: calls whose work overlaps on the GPU
+ * (other streams, other host threads) race and may return wrong numbers.
+ * Returns EINVAL for NULL pointers or bad sizes, ECUDA on a CUDA error, ENAN
+ * (after filling *out) when a density is non-finite. */
+#define LBM_NOALLOC_MAX_NODES 16777216
+LBM_API lbm_status lbm_reduce_fields_noalloc(const float *d_rho_a,
+                                             const float *d_rho_b,
+                                             const float *d_ns, int32_t nx,
+                                             int32_t ny, int32_t nz,
+                                             const int32_t *layers, double G,
+                                             void *cuda_stream,
+                                             lbm_observables *out);
 
 #ifdef __cplusplus
 }

@@ -22,7 +22,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC",
               "-Xcompiler", "-fvisibility=hidden", "-I", INCLUDE, "-I", CSRC]
 
-SOURCES = ["lbm_kernels.cu", "lbm_api.cu"]
+SOURCES = ["lbm_kernels.cu", "lbm_api.cu", "lbm_noalloc.cu"]
 HEADERS = ["lbm_internal.cuh"]
 
 

@@ -18,10 +18,11 @@ import numpy as np
 from . import build as _build
 
 LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_ENAN, LBM_ETIMEOUT, \
-    LBM_ESTATE, LBM_EINTERNAL = range(8)
+    LBM_ESTATE, LBM_EINTERNAL, LBM_ETOOLARGE = range(9)
+LBM_NOALLOC_MAX_NODES = 16777216
 LBM_STORAGE_F32 = 0
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENAN",
-                5: "ETIMEOUT", 6: "ESTATE", 7: "EINTERNAL"}
+                5: "ETIMEOUT", 6: "ESTATE", 7: "EINTERNAL", 8: "ETOOLARGE"}
 
 #: every entry point declared in include/lbm.h
 ABI_SYMBOLS = (
@@ -29,7 +30,7 @@ ABI_SYMBOLS = (
     "lbm_init_equilibrium", "lbm_set_populations", "lbm_get_populations",
     "lbm_set_bc", "lbm_step", "lbm_density", "lbm_collide_stream", "lbm_time",
     "lbm_read_fields", "lbm_reduce", "lbm_sync", "lbm_checkpoint_bytes",
-    "lbm_save", "lbm_load", "lbm_last_error",
+    "lbm_save", "lbm_load", "lbm_last_error", "lbm_reduce_fields_noalloc",
 )
 
 
@@ -92,6 +93,11 @@ def load(path: str | None = None):
         "lbm_save": (ctypes.c_int, [vp, vp, ctypes.c_size_t]),
         "lbm_load": (ctypes.c_int, [vp, vp, ctypes.c_size_t]),
         "lbm_last_error": (ctypes.c_char_p, [vp]),
+        "lbm_reduce_fields_noalloc": (ctypes.c_int, [vp, vp, vp, ctypes.c_int32,
+                                                     ctypes.c_int32, ctypes.c_int32,
+                                                     ctypes.POINTER(ctypes.c_int32),
+                                                     ctypes.c_double, vp,
+                                                     ctypes.POINTER(lbm_observables)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -222,6 +228,21 @@ def lbm_load(ctx, buf: bytes):
 def lbm_last_error(ctx) -> str:
     msg = load().lbm_last_error(ctx)
     return msg.decode() if msg else ""
+
+
+def lbm_reduce_fields_noalloc(d_rho_a: int, d_rho_b: int, d_ns: int, nx: int,
+                              ny: int, nz: int, layers, G: float,
+                              cuda_stream: int):
+    """Allocation-free observables from device density fields (pointers as
+    ints).  Returns (status, lbm_observables); the caller checks the status
+    because there is no context to carry a message."""
+    out = lbm_observables()
+    lay = (ctypes.c_int32 * 6)(*(layers if layers is not None else [0] * 6))
+    st = load().lbm_reduce_fields_noalloc(
+        ctypes.c_void_p(d_rho_a), ctypes.c_void_p(d_rho_b), ctypes.c_void_p(d_ns),
+        nx, ny, nz, lay, float(G), ctypes.c_void_p(cuda_stream),
+        ctypes.byref(out))
+    return st, out
 
 
 # ---- convenience wrapper ------------------------------------------------
