@@ -57,6 +57,9 @@ bool params_valid(const lbm_params *p, const char **why) {
   const long long N = (long long)p->nx * p->ny * p->nz;
   if (N > 2147483647LL) { *why = "nx*ny*nz must be < 2^31"; return false; }
   if ((p->ny + 3) / 4 > 65535 || (p->nz + 1) / 2 > 65535) { *why = "ny or nz too large"; return false; }
+  if (hmcsc::tiling(p->nx, p->ny, p->nz).ntiles * hmcsc::kTile > 2147483647LL) {
+    *why = "lattice too large for 32-node x-tiles"; return false;
+  }
   if (p->storage != LBM_STORAGE_F32) { *why = "unsupported storage"; return false; }
   for (int s = 0; s < 2; ++s)
     if (!(p->tau[s] > 0.5) || !std::isfinite(p->tau[s])) { *why = "tau must be finite and > 1/2"; return false; }
@@ -66,7 +69,15 @@ bool params_valid(const lbm_params *p, const char **why) {
   return true;
 }
 
-size_t padded_stride(const lbm_ctx *c) { return (size_t)c->sp.np; }
+size_t lin_stride(const lbm_ctx *c) { return (size_t)c->sp.nlin; }
+size_t pop_floats(const lbm_ctx *c) { return (size_t)c->sp.ntiles * hmcsc::kTileFloats; }
+
+// Offset (in floats) of slot k of node (x, y, z) in the tiled population
+// layout.
+size_t pop_offset(const lbm_ctx *c, int k, long long x, long long y, long long z) {
+  const long long t = x / hmcsc::kTile + c->sp.ntx * (y + (long long)c->params.ny * z);
+  return (size_t)t * hmcsc::kTileFloats + (size_t)k * hmcsc::kTile + (size_t)(x % hmcsc::kTile);
+}
 
 int parity(const lbm_ctx *c) { return (int)(c->t & 1); }
 
@@ -75,7 +86,7 @@ struct CkptHeader {
   char magic[8];
   int32_t version, storage;
   int32_t nx, ny, nz, pad;
-  int64_t t, np;
+  int64_t t, ntiles;
 };
 const char kMagic[8] = {'H', 'M', 'C', 'S', 'C', 'L', 'B', '1'};
 
@@ -125,7 +136,10 @@ lbm_status lbm_create(const lbm_params *params, void *d_workspace,
   sp.nx = params->nx;
   sp.ny = params->ny;
   sp.nz = params->nz;
-  sp.np = (c->N + 63) / 64 * 64;
+  const hmcsc::Tiling tl = hmcsc::tiling(params->nx, params->ny, params->nz);
+  sp.ntx = (int)tl.ntx;
+  sp.ntiles = tl.ntiles;
+  sp.nlin = tl.nlin;
   for (int s = 0; s < 2; ++s) {
     sp.tau[s] = (float)params->tau[s];
     sp.omega[s] = (float)(1.0 / params->tau[s]);
@@ -137,6 +151,13 @@ lbm_status lbm_create(const lbm_params *params, void *d_workspace,
   c->rho_at = -1;
   c->have_geometry = false;
   c->have_state = false;
+  // Zero the whole workspace once so padding lanes hold defined values.
+  cudaError_t e = cudaMemsetAsync(d_workspace, 0, need, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) {
+    delete c;
+    return LBM_ECUDA;
+  }
   *out = c;
   return LBM_OK;
 }
@@ -153,17 +174,19 @@ lbm_status lbm_set_geometry(lbm_ctx *c, const float *ns, const float *gads2) {
     for (long long n = 0; n < c->N; ++n)
       if (!std::isfinite(gads2[n]))
         return fail(c, LBM_EINVAL, "gads2[%lld] is not finite", n);
-  lbm_status st = upload(c, c->ws.ns, ns, (size_t)c->N);
+  const size_t L = lin_stride(c);
+  lbm_status st = upload(c, c->ws.stage, ns, (size_t)c->N);
   if (st) return st;
   if (gads2) {
-    st = upload(c, c->ws.stage, gads2, (size_t)c->N);
+    st = upload(c, c->ws.stage + L, gads2, (size_t)c->N);
     if (st) return st;
   } else {
-    cudaError_t e = cudaMemsetAsync(c->ws.stage, 0, sizeof(float) * c->N, c->stream);
+    cudaError_t e = cudaMemsetAsync(c->ws.stage + L, 0, sizeof(float) * c->N, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "memset");
   }
-  cudaError_t e = hmcsc::launch_adhesion_source(c->sp, c->ws, c->ws.stage, c->stream);
-  if (e != cudaSuccess) return cuda_fail(c, e, "adhesion source kernel");
+  cudaError_t e = hmcsc::launch_geometry(c->sp, c->ws, c->ws.stage, c->ws.stage + L,
+                                         c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "geometry kernel");
   st = sync_stream(c, "set_geometry");
   if (st) return st;
   c->have_geometry = true;
@@ -179,13 +202,13 @@ lbm_status lbm_init_equilibrium(lbm_ctx *c, const float *rho_a,
     if (!(rho_a[n] > 0.0f) || !(rho_b[n] > 0.0f) || !std::isfinite(rho_a[n]) ||
         !std::isfinite(rho_b[n]))
       return fail(c, LBM_EINVAL, "densities at node %lld must be finite and > 0", n);
-  const size_t np = padded_stride(c);
+  const size_t L = lin_stride(c);
   lbm_status st = upload(c, c->ws.stage, rho_a, (size_t)c->N);
   if (st) return st;
-  st = upload(c, c->ws.stage + np, rho_b, (size_t)c->N);
+  st = upload(c, c->ws.stage + L, rho_b, (size_t)c->N);
   if (st) return st;
   cudaError_t e = hmcsc::launch_init_equilibrium(c->sp, c->ws, c->ws.stage,
-                                                 c->ws.stage + np, c->stream);
+                                                 c->ws.stage + L, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "init kernel");
   st = sync_stream(c, "init_equilibrium");
   if (st) return st;
@@ -209,12 +232,17 @@ lbm_status lbm_set_populations(lbm_ctx *c, const float *f) {
       }
       if (!(r > 0.0f)) return fail(c, LBM_EINVAL, "component %d density <= 0 at node %lld", s, n);
     }
-  const size_t np = padded_stride(c);
-  for (int k = 0; k < 2 * kQ; ++k) {
-    cudaError_t e = cudaMemcpyAsync(c->ws.f + (size_t)k * np, f + (size_t)k * N,
-                                    sizeof(float) * N, cudaMemcpyHostToDevice, c->stream);
-    if (e != cudaSuccess) return cuda_fail(c, e, "host-to-device copy");
-  }
+  std::vector<float> tiled(pop_floats(c), 0.0f);
+  const int nx = c->params.nx, ny = c->params.ny, nz = c->params.nz;
+  for (int k = 0; k < 2 * kQ; ++k)
+    for (int z = 0; z < nz; ++z)
+      for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x)
+          tiled[pop_offset(c, k, x, y, z)] =
+              f[(size_t)k * N + x + (size_t)nx * (y + (size_t)ny * z)];
+  cudaError_t e = cudaMemcpyAsync(c->ws.f, tiled.data(), tiled.size() * sizeof(float),
+                                  cudaMemcpyHostToDevice, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "host-to-device copy");
   lbm_status st = sync_stream(c, "set_populations");
   if (st) return st;
   c->t = 0;
@@ -227,9 +255,8 @@ lbm_status lbm_get_populations(lbm_ctx *c, float *f) {
   if (!c) return LBM_EINVAL;
   if (!f) return fail(c, LBM_EINVAL, "f is NULL");
   if (!c->have_state) return fail(c, LBM_ESTATE, "no state set");
-  const size_t np = padded_stride(c);
   const long long N = c->N;
-  std::vector<float> raw((size_t)2 * kQ * np);
+  std::vector<float> raw(pop_floats(c));
   cudaError_t e = cudaMemcpyAsync(raw.data(), c->ws.f, raw.size() * sizeof(float),
                                   cudaMemcpyDeviceToHost, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "device-to-host copy");
@@ -244,14 +271,13 @@ lbm_status lbm_get_populations(lbm_ctx *c, float *f) {
             const long long n = x + (long long)nx * (y + (long long)ny * z);
             float v;
             if (parity(c) == 0) {
-              v = raw[((size_t)s * kQ + i) * np + n];
+              v = raw[pop_offset(c, s * kQ + i, x, y, z)];
             } else {
               // population i of node n sits in slot opp(i) of node n - c_i
               const int xs = (x - hmcsc::cx(i) + nx) % nx;
               const int ys = (y - hmcsc::cy(i) + ny) % ny;
               const int zs = (z - hmcsc::cz(i) + nz) % nz;
-              const long long m = xs + (long long)nx * (ys + (long long)ny * zs);
-              v = raw[((size_t)s * kQ + hmcsc::opp(i)) * np + m];
+              v = raw[pop_offset(c, s * kQ + hmcsc::opp(i), xs, ys, zs)];
             }
             f[((size_t)s * kQ + i) * N + n] = v;
           }
@@ -323,13 +349,13 @@ lbm_status lbm_read_fields(lbm_ctx *c, float *rho_a, float *rho_b, float *u,
   c->rho_at = c->t;
   e = hmcsc::launch_fields(c->sp, c->ws, parity(c), c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "fields kernel");
-  const size_t np = padded_stride(c);
+  const size_t L = lin_stride(c);
   const size_t bytes = sizeof(float) * (size_t)c->N;
   float *dst[6] = {rho_a, rho_b, u, u ? u + c->N : nullptr,
                    u ? u + 2 * c->N : nullptr, p};
   for (int k = 0; k < 6; ++k) {
     if (!dst[k]) continue;
-    e = cudaMemcpyAsync(dst[k], c->ws.stage + (size_t)k * np, bytes,
+    e = cudaMemcpyAsync(dst[k], c->ws.stage + (size_t)k * L, bytes,
                         cudaMemcpyDeviceToHost, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "device-to-host copy");
   }
@@ -406,7 +432,7 @@ lbm_status lbm_sync(lbm_ctx *c, double timeout_s) {
 
 size_t lbm_checkpoint_bytes(const lbm_ctx *c) {
   if (!c) return 0;
-  return sizeof(CkptHeader) + sizeof(float) * 2 * kQ * (size_t)c->sp.np;
+  return sizeof(CkptHeader) + sizeof(float) * pop_floats(c);
 }
 
 lbm_status lbm_save(lbm_ctx *c, void *host_buf, size_t bytes) {
@@ -423,10 +449,10 @@ lbm_status lbm_save(lbm_ctx *c, void *host_buf, size_t bytes) {
   h.ny = c->params.ny;
   h.nz = c->params.nz;
   h.t = c->t;
-  h.np = c->sp.np;
+  h.ntiles = c->sp.ntiles;
   memcpy(host_buf, &h, sizeof h);
   cudaError_t e = cudaMemcpyAsync((char *)host_buf + sizeof h, c->ws.f,
-                                  sizeof(float) * 2 * kQ * (size_t)c->sp.np,
+                                  sizeof(float) * pop_floats(c),
                                   cudaMemcpyDeviceToHost, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "device-to-host copy");
   return sync_stream(c, "save");
@@ -441,12 +467,12 @@ lbm_status lbm_load(lbm_ctx *c, const void *host_buf, size_t bytes) {
   if (memcmp(h.magic, kMagic, 8) != 0 || h.version != 1)
     return fail(c, LBM_EINVAL, "not a checkpoint of this library");
   if (h.nx != c->params.nx || h.ny != c->params.ny || h.nz != c->params.nz ||
-      h.storage != c->params.storage || h.np != c->sp.np || h.t < 0)
+      h.storage != c->params.storage || h.ntiles != c->sp.ntiles || h.t < 0)
     return fail(c, LBM_EINVAL, "checkpoint lattice or storage differs");
   if (bytes < lbm_checkpoint_bytes(c))
     return fail(c, LBM_EINVAL, "checkpoint truncated");
   cudaError_t e = cudaMemcpyAsync(c->ws.f, (const char *)host_buf + sizeof h,
-                                  sizeof(float) * 2 * kQ * (size_t)c->sp.np,
+                                  sizeof(float) * pop_floats(c),
                                   cudaMemcpyHostToDevice, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "host-to-device copy");
   lbm_status st = sync_stream(c, "load");

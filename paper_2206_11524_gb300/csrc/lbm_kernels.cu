@@ -6,71 +6,88 @@
 //                    velocity (Eq. 6), equilibrium (Eq. A.3), gray collision
 //                    with partial bounce-back (Eq. 1), in-place streaming and
 //                    the density reservoirs (Sec. 4)
-// Populations live in one buffer per component in structure-of-arrays form
-// f[sigma][i][n] and stream in place with the AA pattern:
+//
+// Populations live in 32-node x-tiles (see lbm_internal.cuh) and stream in
+// place with the AA pattern:
 //   even t: node n reads slot i at n, writes its post-collision f_i to slot
 //           opp(i) at n (population i of node n + c_i at t + 1);
 //   odd t:  node n reads population i from slot opp(i) at n - c_i, writes
 //           its post-collision f_i to slot i at n + c_i.
 // Every (slot, node) a thread writes is one it read itself, so the update is
 // race-free in place, and after an odd step the layout is natural again.
+// One warp is one tile: on even steps all 38 accesses of a thread are one
+// pointer plus a constant; on odd steps there is one pointer per neighbour
+// offset, shared by the loads and the stores at that offset.
 #include "lbm_internal.cuh"
 
 namespace hmcsc {
 namespace {
 
-constexpr int kBX = 32, kBY = 4, kBZ = 2;
+constexpr int kBY = 4, kBZ = 2;                 // block = 32 x kBY x kBZ nodes
+constexpr int kThreads = kTile * kBY * kBZ;     // 256
 
-// Periodic neighbourhood of one node: wrapped coordinates and offsets.
-struct Nbr {
-  int xw[3], yw[3], zw[3];
-  int row[3];  // yw * nx
-  int pln[3];  // zw * nx * ny
-  __device__ __forceinline__ int at(int dx, int dy, int dz) const {
-    return xw[dx + 1] + row[dy + 1] + pln[dz + 1];
+// Periodic neighbourhood of one node in tile coordinates.
+struct Geo {
+  int tx[3], ln[3];  // tile-x index and lane of x-1, x, x+1
+  int yw[3], zw[3];  // y-1..y+1, z-1..z+1 (wrapped)
+  int tr[3][3];      // first tile of row (y', z'): ntx * (y' + ny * z')
+  __device__ __forceinline__ int tile(int dx, int dy, int dz) const {
+    return tr[dy + 1][dz + 1] + tx[dx + 1];
   }
+  // tiled node index of x + (dx, dy, dz)
+  __device__ __forceinline__ int node(int dx, int dy, int dz) const {
+    return tile(dx, dy, dz) * kTile + ln[dx + 1];
+  }
+  __device__ __forceinline__ int xof(int dx) const { return tx[dx + 1] * kTile + ln[dx + 1]; }
 };
 
-__device__ __forceinline__ Nbr make_nbr(const StepParams &p, int x, int y,
+__device__ __forceinline__ Geo make_geo(const StepParams &p, int x, int y,
                                         int z) {
-  Nbr b;
-  b.xw[0] = x == 0 ? p.nx - 1 : x - 1;
-  b.xw[1] = x;
-  b.xw[2] = x == p.nx - 1 ? 0 : x + 1;
-  b.yw[0] = y == 0 ? p.ny - 1 : y - 1;
-  b.yw[1] = y;
-  b.yw[2] = y == p.ny - 1 ? 0 : y + 1;
-  b.zw[0] = z == 0 ? p.nz - 1 : z - 1;
-  b.zw[1] = z;
-  b.zw[2] = z == p.nz - 1 ? 0 : z + 1;
-  const int nxy = p.nx * p.ny;
+  Geo g;
+  const int xm = x == 0 ? p.nx - 1 : x - 1;
+  const int xp = x == p.nx - 1 ? 0 : x + 1;
+  g.tx[0] = xm / kTile; g.ln[0] = xm % kTile;
+  g.tx[1] = x / kTile;  g.ln[1] = x % kTile;
+  g.tx[2] = xp / kTile; g.ln[2] = xp % kTile;
+  g.yw[0] = y == 0 ? p.ny - 1 : y - 1;
+  g.yw[1] = y;
+  g.yw[2] = y == p.ny - 1 ? 0 : y + 1;
+  g.zw[0] = z == 0 ? p.nz - 1 : z - 1;
+  g.zw[1] = z;
+  g.zw[2] = z == p.nz - 1 ? 0 : z + 1;
 #pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    b.row[k] = b.yw[k] * p.nx;
-    b.pln[k] = b.zw[k] * nxy;
-  }
-  return b;
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) g.tr[a][b] = p.ntx * (g.yw[a] + p.ny * g.zw[b]);
+  return g;
 }
 
-__device__ __forceinline__ const float *slot(const float *f, long long np,
-                                             int s, int i) {
-  return f + (size_t)(s * kQ + i) * (size_t)np;
-}
-__device__ __forceinline__ float *slot(float *f, long long np, int s, int i) {
-  return f + (size_t)(s * kQ + i) * (size_t)np;
+// Lane-adjusted base of the tile holding node x + (dx, dy, dz): slot k of
+// that node is at base[k * 32].
+__device__ __forceinline__ float *pop_base(float *f, const Geo &g, int dx,
+                                           int dy, int dz) {
+  return f + (size_t)g.tile(dx, dy, dz) * kTileFloats + g.ln[dx + 1];
 }
 
-// The 19 populations of component s at node n at the current time step.
+// The 19 populations of both components at the current time step.
 template <int PARITY>
-__device__ __forceinline__ void load_pops(const float *__restrict__ f,
-                                          long long np, const Nbr &nb, int n,
-                                          int s, float (&v)[kQ]) {
+__device__ __forceinline__ void load_pops(float *f, const Geo &g,
+                                          float (&v1)[kQ], float (&v2)[kQ]) {
+  if (PARITY == 0) {
+    const float *b = pop_base(f, g, 0, 0, 0);
 #pragma unroll
-  for (int i = 0; i < kQ; ++i) {
-    if (PARITY == 0)
-      v[i] = slot(f, np, s, i)[n];
-    else
-      v[i] = slot(f, np, s, opp(i))[nb.at(-cx(i), -cy(i), -cz(i))];
+    for (int i = 0; i < kQ; ++i) {
+      v1[i] = b[i * kTile];
+      v2[i] = b[(kQ + i) * kTile];
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) {
+      // population i of node x sits in slot opp(i) of node x - c_i
+      const float *b = pop_base(f, g, -cx(i), -cy(i), -cz(i));
+      v1[i] = b[opp(i) * kTile];
+      v2[i] = b[(kQ + opp(i)) * kTile];
+    }
   }
 }
 
@@ -104,13 +121,13 @@ __device__ __forceinline__ void first_moment(const float (&v)[kQ],
 __device__ __forceinline__ void force_per_mass(const StepParams &p,
                                                const float2 *__restrict__ rho,
                                                const float *__restrict__ ads,
-                                               const Nbr &nb, float rho_tot,
+                                               const Geo &g, float rho_tot,
                                                float (&g1)[3], float (&g2)[3]) {
   float s1[3] = {0.f, 0.f, 0.f}, s2[3] = {0.f, 0.f, 0.f}, sa[3] = {0.f, 0.f, 0.f};
 #pragma unroll
   for (int i = 1; i <= 9; ++i) {
-    const int mp = nb.at(cx(i), cy(i), cz(i));
-    const int mm = nb.at(-cx(i), -cy(i), -cz(i));
+    const int mp = g.node(cx(i), cy(i), cz(i));
+    const int mm = g.node(-cx(i), -cy(i), -cz(i));
     const float2 rp = __ldg(&rho[mp]);
     const float2 rm = __ldg(&rho[mm]);
     const float ap = __ldg(&ads[mp]);
@@ -145,36 +162,37 @@ __device__ __forceinline__ int res_face(const StepParams &p, int x, int y,
   return face;
 }
 
-// True when some neighbour x + c_i (periodic) may lie in a reservoir.
-__device__ __forceinline__ bool near_reservoir(const StepParams &p, int x,
-                                               int y, int z) {
+// Does some node of the box [xlo,xhi] x [ylo,yhi] x [zlo,zhi] have a
+// (periodic) neighbour inside a reservoir?  Uniform over a block.
+__device__ __forceinline__ bool box_near_reservoir(const StepParams &p, int xlo,
+                                                   int xhi, int ylo, int yhi,
+                                                   int zlo, int zhi) {
+  if (!p.res.any) return false;
   const int *L = p.res.layers;
-  bool nx_ = (L[0] && (x <= L[0] || x == p.nx - 1)) ||
-             (L[1] && (x >= p.nx - 1 - L[1] || x == 0));
-  bool ny_ = (L[2] && (y <= L[2] || y == p.ny - 1)) ||
-             (L[3] && (y >= p.ny - 1 - L[3] || y == 0));
-  bool nz_ = (L[4] && (z <= L[4] || z == p.nz - 1)) ||
-             (L[5] && (z >= p.nz - 1 - L[5] || z == 0));
-  return nx_ || ny_ || nz_;
+  const bool bx = (L[0] && (xlo <= L[0] || xhi >= p.nx - 1)) ||
+                  (L[1] && (xhi >= p.nx - 1 - L[1] || xlo == 0));
+  const bool by = (L[2] && (ylo <= L[2] || yhi >= p.ny - 1)) ||
+                  (L[3] && (yhi >= p.ny - 1 - L[3] || ylo == 0));
+  const bool bz = (L[4] && (zlo <= L[4] || zhi >= p.nz - 1)) ||
+                  (L[5] && (zhi >= p.nz - 1 - L[5] || zlo == 0));
+  return bx || by || bz;
 }
 
-// Store the post-collision population i of component s of node n; it becomes
-// population i of node n + c_i at t + 1.  If that node is in a reservoir, the
-// prescribed equilibrium w_i rho_res at rest is stored instead (the reset of
-// Sec. 4, applied as the population arrives).
-template <int PARITY>
-__device__ __forceinline__ void put(float *__restrict__ f, const StepParams &p,
-                                   const Nbr &nb, int n, int s, int i,
-                                   float val, bool near) {
-  if (near) {
-    const int face = res_face(p, nb.xw[cx(i) + 1], nb.yw[cy(i) + 1],
-                              nb.zw[cz(i) + 1]);
+// Store the post-collision population i of component s; it becomes
+// population i of node x + c_i at t + 1.  With RES, a destination inside a
+// reservoir receives the prescribed equilibrium w_i rho_res at rest instead
+// (the reset of Sec. 4, applied as the population arrives).
+template <int PARITY, bool RES>
+__device__ __forceinline__ void put(const StepParams &p, float *f,
+                                    const Geo &g, int s, int i, float val) {
+  if (RES) {
+    const int face = res_face(p, g.xof(cx(i)), g.yw[1 + cy(i)], g.zw[1 + cz(i)]);
     if (face >= 0) val = wgt(i) * p.res.rho[face][s];
   }
   if (PARITY == 0)
-    slot(f, p.np, s, opp(i))[n] = val;
+    pop_base(f, g, 0, 0, 0)[(s * kQ + opp(i)) * kTile] = val;
   else
-    slot(f, p.np, s, i)[nb.at(cx(i), cy(i), cz(i))] = val;
+    pop_base(f, g, cx(i), cy(i), cz(i))[(s * kQ + i) * kTile] = val;
 }
 
 // Eq. 1 for one component: (1 - n_s)[f_i - (f_i - f^eq_i)/tau] + n_s f_opp(i)
@@ -182,12 +200,11 @@ __device__ __forceinline__ void put(float *__restrict__ f, const StepParams &p,
 // The rest population's equilibrium is taken as rho_s minus the other 18
 // (sum_i f^eq_i = rho_s holds exactly for Eq. A.3 on D3Q19), which keeps the
 // rounding of the float weights from leaking mass step after step.
-template <int PARITY>
-__device__ __forceinline__ void collide_put(float *__restrict__ f,
-                                            const StepParams &p, const Nbr &nb,
-                                            int n, int s, const float (&v)[kQ],
-                                            float rho_s, const float (&u)[3],
-                                            float nsx, bool near) {
+template <int PARITY, bool RES>
+__device__ __forceinline__ void collide_put(const StepParams &p, float *f,
+                                            const Geo &g, int s,
+                                            const float (&v)[kQ], float rho_s,
+                                            const float (&u)[3], float nsx) {
   const float om = p.omega[s];
   const float a = (1.0f - nsx) * (1.0f - om);
   const float b = (1.0f - nsx) * om;
@@ -202,50 +219,27 @@ __device__ __forceinline__ void collide_put(float *__restrict__ f,
     const float odd = wr * 3.0f * cu;
     const float fe_i = even + odd, fe_j = even - odd;
     moving += fe_i + fe_j;
-    put<PARITY>(f, p, nb, n, s, i, a * v[i] + b * fe_i + nsx * v[j], near);
-    put<PARITY>(f, p, nb, n, s, j, a * v[j] + b * fe_j + nsx * v[i], near);
+    put<PARITY, RES>(p, f, g, s, i, a * v[i] + b * fe_i + nsx * v[j]);
+    put<PARITY, RES>(p, f, g, s, j, a * v[j] + b * fe_j + nsx * v[i]);
   }
   const float fe_0 = rho_s - moving;
-  put<PARITY>(f, p, nb, n, s, 0, a * v[0] + b * fe_0 + nsx * v[0], near);
+  put<PARITY, RES>(p, f, g, s, 0, a * v[0] + b * fe_0 + nsx * v[0]);
 }
 
-template <int PARITY>
-__global__ void __launch_bounds__(kBX * kBY * kBZ)
-    k_density(StepParams p, Workspace w) {
-  const int x = blockIdx.x * kBX + threadIdx.x;
-  const int y = blockIdx.y * kBY + threadIdx.y;
-  const int z = blockIdx.z * kBZ + threadIdx.z;
-  if (x >= p.nx || y >= p.ny || z >= p.nz) return;
-  const Nbr nb = make_nbr(p, x, y, z);
-  const int n = nb.at(0, 0, 0);
-  float v[kQ];
-  load_pops<PARITY>(w.f, p.np, nb, n, 0, v);
-  const float r1 = sum19(v);
-  load_pops<PARITY>(w.f, p.np, nb, n, 1, v);
-  const float r2 = sum19(v);
-  w.rho[n] = make_float2(r1, r2);
-}
-
-template <int PARITY>
-__global__ void __launch_bounds__(kBX * kBY * kBZ)
-    k_collide_stream(StepParams p, Workspace w) {
-  const int x = blockIdx.x * kBX + threadIdx.x;
-  const int y = blockIdx.y * kBY + threadIdx.y;
-  const int z = blockIdx.z * kBZ + threadIdx.z;
-  if (x >= p.nx || y >= p.ny || z >= p.nz) return;
-  const Nbr nb = make_nbr(p, x, y, z);
-  const int n = nb.at(0, 0, 0);
-
+template <int PARITY, bool RES>
+__device__ __forceinline__ void collide_body(const StepParams &p,
+                                             const Workspace &w, int x, int y,
+                                             int z) {
+  const Geo g = make_geo(p, x, y, z);
   float f1[kQ], f2[kQ];
-  load_pops<PARITY>(w.f, p.np, nb, n, 0, f1);
-  load_pops<PARITY>(w.f, p.np, nb, n, 1, f2);
+  load_pops<PARITY>(w.f, g, f1, f2);
   const float r1 = sum19(f1), r2 = sum19(f2);
   float j1[3], j2[3];
   first_moment(f1, j1);
   first_moment(f2, j2);
 
   float g1[3], g2[3];
-  force_per_mass(p, w.rho, w.ads, nb, r1 + r2, g1, g2);
+  force_per_mass(p, w.rho, w.ads, g, r1 + r2, g1, g2);
 
   // Eq. 6: common velocity sum_s j_s/tau_s / sum_s rho_s/tau_s, then the
   // Shan-Chen shift tau_s F_tot,s / rho_s = tau_s g_s.
@@ -258,43 +252,89 @@ __global__ void __launch_bounds__(kBX * kBY * kBZ)
     u2[d] = uc + p.tau[1] * g2[d];
   }
 
-  const float nsx = w.ns[n];
-  const bool near = p.res.any && near_reservoir(p, x, y, z);
-  collide_put<PARITY>(w.f, p, nb, n, 0, f1, r1, u1, nsx, near);
-  collide_put<PARITY>(w.f, p, nb, n, 1, f2, r2, u2, nsx, near);
+  const float nsx = w.ns[g.node(0, 0, 0)];
+  collide_put<PARITY, RES>(p, w.f, g, 0, f1, r1, u1, nsx);
+  collide_put<PARITY, RES>(p, w.f, g, 1, f2, r2, u2, nsx);
 }
 
-// Macroscopic fields of the current state into the staging planes:
+__device__ __forceinline__ void block_coords(int &x, int &y, int &z) {
+  x = blockIdx.x * kTile + threadIdx.x;
+  y = blockIdx.y * kBY + threadIdx.y;
+  z = blockIdx.z * kBZ + threadIdx.z;
+}
+
+template <int PARITY>
+__global__ void __launch_bounds__(kThreads) k_density(StepParams p, Workspace w) {
+  int x, y, z;
+  block_coords(x, y, z);
+  if (x >= p.nx || y >= p.ny || z >= p.nz) return;
+  const Geo g = make_geo(p, x, y, z);
+  float v1[kQ], v2[kQ];
+  load_pops<PARITY>(w.f, g, v1, v2);
+  w.rho[g.node(0, 0, 0)] = make_float2(sum19(v1), sum19(v2));
+}
+
+// Register budget per parity: the even step keeps one tile pointer and fits
+// 80 registers (3 blocks / SM); the odd step keeps one pointer per neighbour
+// offset and gets 128 (2 blocks / SM) so that nothing spills.
+#ifndef HMCSC_MINB_EVEN
+#define HMCSC_MINB_EVEN 3
+#endif
+#ifndef HMCSC_MINB_ODD
+#define HMCSC_MINB_ODD 2
+#endif
+template <int PARITY>
+__global__ void __launch_bounds__(kThreads, PARITY == 0 ? HMCSC_MINB_EVEN : HMCSC_MINB_ODD)
+    k_collide_stream(StepParams p, Workspace w) {
+  int x, y, z;
+  block_coords(x, y, z);
+  const int xlo = blockIdx.x * kTile, ylo = blockIdx.y * kBY, zlo = blockIdx.z * kBZ;
+  const bool res = box_near_reservoir(p, xlo, min(xlo + kTile - 1, p.nx - 1), ylo,
+                                      min(ylo + kBY - 1, p.ny - 1), zlo,
+                                      min(zlo + kBZ - 1, p.nz - 1));
+  if (x >= p.nx || y >= p.ny || z >= p.nz) return;
+  if (res)
+    collide_body<PARITY, true>(p, w, x, y, z);
+  else
+    collide_body<PARITY, false>(p, w, x, y, z);
+}
+
+// Macroscopic fields of the current state into the linear staging planes:
 // rho_1, rho_2, u_macro (Eq. 7) x, y, z, p (Eq. A.6).
 template <int PARITY>
-__global__ void __launch_bounds__(kBX * kBY * kBZ)
-    k_fields(StepParams p, Workspace w) {
-  const int x = blockIdx.x * kBX + threadIdx.x;
-  const int y = blockIdx.y * kBY + threadIdx.y;
-  const int z = blockIdx.z * kBZ + threadIdx.z;
+__global__ void __launch_bounds__(kThreads) k_fields(StepParams p, Workspace w) {
+  int x, y, z;
+  block_coords(x, y, z);
   if (x >= p.nx || y >= p.ny || z >= p.nz) return;
-  const Nbr nb = make_nbr(p, x, y, z);
-  const int n = nb.at(0, 0, 0);
+  const Geo g = make_geo(p, x, y, z);
   float f1[kQ], f2[kQ];
-  load_pops<PARITY>(w.f, p.np, nb, n, 0, f1);
-  load_pops<PARITY>(w.f, p.np, nb, n, 1, f2);
+  load_pops<PARITY>(w.f, g, f1, f2);
   const float r1 = sum19(f1), r2 = sum19(f2);
   float j1[3], j2[3];
   first_moment(f1, j1);
   first_moment(f2, j2);
   float g1[3], g2[3];
   const float rho = r1 + r2;
-  force_per_mass(p, w.rho, w.ads, nb, rho, g1, g2);
-  const float fluid = 1.0f - w.ns[n];
-  const long long np = p.np;
+  force_per_mass(p, w.rho, w.ads, g, rho, g1, g2);
+  const float fluid = 1.0f - w.ns[g.node(0, 0, 0)];
+  const long long L = p.nlin;
+  const long long n = x + (long long)p.nx * (y + (long long)p.ny * z);
   w.stage[n] = r1;
-  w.stage[np + n] = r2;
+  w.stage[L + n] = r2;
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     const float m = (j1[d] + 0.5f * r1 * g1[d]) + (j2[d] + 0.5f * r2 * g2[d]);
-    w.stage[(2 + d) * np + n] = fluid * m / rho;
+    w.stage[(2 + d) * L + n] = fluid * m / rho;
   }
-  w.stage[5 * np + n] = (rho + p.G * r1 * r2) * (1.0f / 3.0f);
+  w.stage[5 * L + n] = (rho + p.G * r1 * r2) * (1.0f / 3.0f);
+}
+
+// Tiled node index of linear node n = x + nx (y + ny z).
+__device__ __forceinline__ long long tiled_of_linear(const StepParams &p,
+                                                     long long n) {
+  const int x = (int)(n % p.nx);
+  const long long yz = n / p.nx;
+  return (yz * p.ntx + x / kTile) * kTile + x % kTile;
 }
 
 __global__ void k_init_equilibrium(StepParams p, Workspace w,
@@ -303,21 +343,29 @@ __global__ void k_init_equilibrium(StepParams p, Workspace w,
   const long long N = (long long)p.nx * p.ny * p.nz;
   for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
        n += (long long)gridDim.x * blockDim.x) {
+    const long long tn = tiled_of_linear(p, n);
+    float *b = w.f + (tn / kTile) * kTileFloats + tn % kTile;
     const float r1 = rho1[n], r2 = rho2[n];
 #pragma unroll
     for (int i = 0; i < kQ; ++i) {
-      slot(w.f, p.np, 0, i)[n] = wgt(i) * r1;
-      slot(w.f, p.np, 1, i)[n] = wgt(i) * r2;
+      b[i * kTile] = wgt(i) * r1;
+      b[(kQ + i) * kTile] = wgt(i) * r2;
     }
   }
 }
 
-__global__ void k_adhesion_source(StepParams p, Workspace w,
-                                  const float *__restrict__ gads2) {
+// n_s and the adhesion source a = G_ads,2 n_s in tiled order.
+__global__ void k_geometry(StepParams p, Workspace w,
+                           const float *__restrict__ ns_lin,
+                           const float *__restrict__ gads2_lin) {
   const long long N = (long long)p.nx * p.ny * p.nz;
   for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
-       n += (long long)gridDim.x * blockDim.x)
-    w.ads[n] = gads2[n] * w.ns[n];
+       n += (long long)gridDim.x * blockDim.x) {
+    const long long tn = tiled_of_linear(p, n);
+    const float s = ns_lin[n];
+    w.ns[tn] = s;
+    w.ads[tn] = gads2_lin[n] * s;
+  }
 }
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -332,14 +380,17 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce(StepParams p,
   double acc[kRedK];
 #pragma unroll
   for (int k = 0; k < kRedK; ++k) acc[k] = 0.0;
-  const long long N = (long long)p.nx * p.ny * p.nz;
+  const long long NT = p.ntiles * kTile;
   const int *L = p.res.layers;
-  for (long long n = blockIdx.x * (long long)kRedThreads + threadIdx.x; n < N;
-       n += (long long)kRedBlocks * kRedThreads) {
-    const int x = (int)(n % p.nx);
-    const int y = (int)((n / p.nx) % p.ny);
-    const int z = (int)(n / ((long long)p.nx * p.ny));
-    const float2 r = w.rho[n];
+  for (long long tn = blockIdx.x * (long long)kRedThreads + threadIdx.x; tn < NT;
+       tn += (long long)kRedBlocks * kRedThreads) {
+    const long long t = tn / kTile;
+    const int x = (int)(t % p.ntx) * kTile + (int)(tn % kTile);
+    if (x >= p.nx) continue;
+    const long long yz = t / p.ntx;
+    const int y = (int)(yz % p.ny);
+    const int z = (int)(yz / p.ny);
+    const float2 r = w.rho[tn];
     acc[0] += r.x;
     acc[1] += r.y;
     if (!isfinite(r.x) || !isfinite(r.y)) acc[10] += 1.0;
@@ -356,7 +407,7 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce(StepParams p,
         acc[4 + k] += pr;
       }
     if (!any) {
-      const double wgt_fluid = 1.0 - (double)w.ns[n];
+      const double wgt_fluid = 1.0 - (double)w.ns[tn];
       acc[3] += wgt_fluid;
       if (r.x >= 0.5f) acc[2] += wgt_fluid;
     }
@@ -385,8 +436,7 @@ __global__ void k_reduce_final(Workspace w) {
 }
 
 dim3 node_grid(const StepParams &p) {
-  return dim3((p.nx + kBX - 1) / kBX, (p.ny + kBY - 1) / kBY,
-              (p.nz + kBZ - 1) / kBZ);
+  return dim3(p.ntx, (p.ny + kBY - 1) / kBY, (p.nz + kBZ - 1) / kBZ);
 }
 
 int flat_blocks(const StepParams &p) {
@@ -399,19 +449,19 @@ int flat_blocks(const StepParams &p) {
 
 size_t workspace_bytes(long long nx, long long ny, long long nz, Workspace *out,
                        char *base) {
-  const long long N = nx * ny * nz;
-  const long long np = (N + 63) / 64 * 64;
+  const Tiling t = tiling(nx, ny, nz);
+  const size_t nt = (size_t)t.ntiles * kTile;
   size_t off = 0;
   auto take = [&](size_t bytes) {
     size_t at = off;
     off += (bytes + 255) / 256 * 256;
     return at;
   };
-  size_t o_f = take(sizeof(float) * 2 * kQ * (size_t)np);
-  size_t o_rho = take(sizeof(float2) * (size_t)np);
-  size_t o_ns = take(sizeof(float) * (size_t)np);
-  size_t o_ads = take(sizeof(float) * (size_t)np);
-  size_t o_stage = take(sizeof(float) * 6 * (size_t)np);
+  size_t o_f = take(sizeof(float) * (size_t)t.ntiles * kTileFloats);
+  size_t o_rho = take(sizeof(float2) * nt);
+  size_t o_ns = take(sizeof(float) * nt);
+  size_t o_ads = take(sizeof(float) * nt);
+  size_t o_stage = take(sizeof(float) * 6 * (size_t)t.nlin);
   size_t o_red = take(sizeof(double) * (kRedBlocks + 1) * kRedK);
   if (out) {
     out->f = (float *)(base + o_f);
@@ -431,15 +481,16 @@ cudaError_t launch_init_equilibrium(const StepParams &p, const Workspace &w,
   return cudaGetLastError();
 }
 
-cudaError_t launch_adhesion_source(const StepParams &p, const Workspace &w,
-                                   const float *gads2, cudaStream_t s) {
-  k_adhesion_source<<<flat_blocks(p), 256, 0, s>>>(p, w, gads2);
+cudaError_t launch_geometry(const StepParams &p, const Workspace &w,
+                            const float *ns_lin, const float *gads2_lin,
+                            cudaStream_t s) {
+  k_geometry<<<flat_blocks(p), 256, 0, s>>>(p, w, ns_lin, gads2_lin);
   return cudaGetLastError();
 }
 
 cudaError_t launch_density(const StepParams &p, const Workspace &w, int parity,
                            cudaStream_t s) {
-  const dim3 block(kBX, kBY, kBZ);
+  const dim3 block(kTile, kBY, kBZ);
   if (parity == 0)
     k_density<0><<<node_grid(p), block, 0, s>>>(p, w);
   else
@@ -449,7 +500,7 @@ cudaError_t launch_density(const StepParams &p, const Workspace &w, int parity,
 
 cudaError_t launch_collide_stream(const StepParams &p, const Workspace &w,
                                   int parity, cudaStream_t s) {
-  const dim3 block(kBX, kBY, kBZ);
+  const dim3 block(kTile, kBY, kBZ);
   if (parity == 0)
     k_collide_stream<0><<<node_grid(p), block, 0, s>>>(p, w);
   else
@@ -459,7 +510,7 @@ cudaError_t launch_collide_stream(const StepParams &p, const Workspace &w,
 
 cudaError_t launch_fields(const StepParams &p, const Workspace &w, int parity,
                           cudaStream_t s) {
-  const dim3 block(kBX, kBY, kBZ);
+  const dim3 block(kTile, kBY, kBZ);
   if (parity == 0)
     k_fields<0><<<node_grid(p), block, 0, s>>>(p, w);
   else

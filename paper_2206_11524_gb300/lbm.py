@@ -65,7 +65,7 @@ def load(path: str | None = None):
     global _lib
     if _lib is not None:
         return _lib
-    path = path or _LIBPATH
+    path = path or os.environ.get("HMCSC_LBM_LIBRARY") or _LIBPATH
     if not os.path.exists(path):
         raise ImportError(
             f"CUDA library not built: {path} is missing "
