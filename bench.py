@@ -340,7 +340,7 @@ def run_gpu(args, world, rank, local):
         "step_hbm_gbs": (BYTES_DENSITY + BYTES_COLLIDE) * N / (ms_max / K / 1e3) / 1e9,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d / K,
                 "d2h_bytes_per_step": d2h / K},
-        "gpu_launches": 2 * K,
+        "gpu_launches": 2 * K,   # density pass + fused pass per step
         "clocks": clk,
         "cpu_baseline": cpu,
     }

@@ -122,8 +122,9 @@ LBM_API lbm_status lbm_get_populations(lbm_ctx *ctx, float *f);
  * outermost layers of face `face` (0..5 = -x,+x,-y,+y,-z,+z) hold
  * f^eq(rho_a / rho_b, u = 0).  layers = 0 removes it.  Where two faces'
  * layers overlap, the higher face index wins.  May be called between steps
- * (an inlet density ramp).  EINVAL if the layers exceed the axis length or a
- * density is not positive. */
+ * (an inlet density ramp): the new values reset the layers at the end of the
+ * next step.  The initial state of the layers is whatever was set.  EINVAL
+ * if the layers exceed the axis length or a density is not positive. */
 LBM_API lbm_status lbm_set_bc(lbm_ctx *ctx, int face, int layers, double rho_a,
                       double rho_b);
 

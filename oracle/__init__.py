@@ -157,6 +157,12 @@ class Sim:
                                      _ptr(self.f))
         self.t = 0
 
+    def set_reservoirs(self, reservoirs: dict):
+        """Change the reservoir faces; the new values reset the layers at the
+        end of the next step (an inlet density ramp, Sec. 4)."""
+        self.p.reservoirs = dict(reservoirs)
+        self._cp = self.p.c_struct()
+
     def set_populations(self, f):
         self.f[...] = np.asarray(f, dtype=np.float64).reshape(self.f.shape)
 

@@ -22,7 +22,8 @@ using hmcsc::kRedK;
 
 struct lbm_ctx {
   lbm_params params;
-  hmcsc::StepParams sp;
+  hmcsc::StepParams sp;   // sp.res: reservoirs applied at the end of the last step
+  hmcsc::Reservoirs res_current;  // reservoirs set by lbm_set_bc (next steps)
   hmcsc::Workspace ws;
   cudaStream_t stream;
   long long N;
@@ -57,7 +58,9 @@ bool params_valid(const lbm_params *p, const char **why) {
   const long long N = (long long)p->nx * p->ny * p->nz;
   if (N > 2147483647LL) { *why = "nx*ny*nz must be < 2^31"; return false; }
   if ((p->ny + 3) / 4 > 65535 || (p->nz + 1) / 2 > 65535) { *why = "ny or nz too large"; return false; }
-  if (hmcsc::tiling(p->nx, p->ny, p->nz).ntiles * hmcsc::kTile > 2147483647LL) {
+  const hmcsc::Tiling tl = hmcsc::tiling(p->nx, p->ny, p->nz);
+  if (tl.ntiles * hmcsc::kTile > 2147483647LL ||
+      tl.ntiles * (long long)hmcsc::kTileFloats > 4294967295LL) {
     *why = "lattice too large for 32-node x-tiles"; return false;
   }
   if (p->storage != LBM_STORAGE_F32) { *why = "unsupported storage"; return false; }
@@ -81,14 +84,28 @@ size_t pop_offset(const lbm_ctx *c, int k, long long x, long long y, long long z
 
 int parity(const lbm_ctx *c) { return (int)(c->t & 1); }
 
+// Reservoir face of node (x, y, z) for reservoir set r (higher face wins).
+int reservoir_face(const hmcsc::Reservoirs &r, const lbm_params &p, int x,
+                   int y, int z) {
+  int face = -1;
+  if (r.layers[0] && x < r.layers[0]) face = 0;
+  if (r.layers[1] && x >= p.nx - r.layers[1]) face = 1;
+  if (r.layers[2] && y < r.layers[2]) face = 2;
+  if (r.layers[3] && y >= p.ny - r.layers[3]) face = 3;
+  if (r.layers[4] && z < r.layers[4]) face = 4;
+  if (r.layers[5] && z >= p.nz - r.layers[5]) face = 5;
+  return face;
+}
+
 // Checkpoint header.
 struct CkptHeader {
   char magic[8];
   int32_t version, storage;
   int32_t nx, ny, nz, pad;
   int64_t t, ntiles;
+  hmcsc::Reservoirs applied;  // reservoirs whose reset ended step t
 };
-const char kMagic[8] = {'H', 'M', 'C', 'S', 'C', 'L', 'B', '1'};
+const char kMagic[8] = {'H', 'M', 'C', 'S', 'C', 'L', 'B', '2'};
 
 lbm_status sync_stream(lbm_ctx *c, const char *what) {
   cudaError_t e = cudaStreamSynchronize(c->stream);
@@ -147,6 +164,7 @@ lbm_status lbm_create(const lbm_params *params, void *d_workspace,
   sp.G = (float)params->G;
   for (int d = 0; d < 3; ++d) sp.F[d] = (float)params->F_ext[d];
   memset(&sp.res, 0, sizeof sp.res);
+  memset(&c->res_current, 0, sizeof c->res_current);
   c->t = 0;
   c->rho_at = -1;
   c->have_geometry = false;
@@ -212,6 +230,7 @@ lbm_status lbm_init_equilibrium(lbm_ctx *c, const float *rho_a,
   if (e != cudaSuccess) return cuda_fail(c, e, "init kernel");
   st = sync_stream(c, "init_equilibrium");
   if (st) return st;
+  memset(&c->sp.res, 0, sizeof c->sp.res);
   c->t = 0;
   c->rho_at = -1;
   c->have_state = true;
@@ -245,6 +264,7 @@ lbm_status lbm_set_populations(lbm_ctx *c, const float *f) {
   if (e != cudaSuccess) return cuda_fail(c, e, "host-to-device copy");
   lbm_status st = sync_stream(c, "set_populations");
   if (st) return st;
+  memset(&c->sp.res, 0, sizeof c->sp.res);
   c->t = 0;
   c->rho_at = -1;
   c->have_state = true;
@@ -279,6 +299,11 @@ lbm_status lbm_get_populations(lbm_ctx *c, float *f) {
               const int zs = (z - hmcsc::cz(i) + nz) % nz;
               v = raw[pop_offset(c, s * kQ + hmcsc::opp(i), xs, ys, zs)];
             }
+            if (c->sp.res.any) {
+              // a node inside a reservoir holds w_i rho_res (see the kernels)
+              const int face = reservoir_face(c->sp.res, c->params, x, y, z);
+              if (face >= 0) v = hmcsc::wgt(i) * c->sp.res.rho[face][s];
+            }
             f[((size_t)s * kQ + i) * N + n] = v;
           }
   return LBM_OK;
@@ -293,12 +318,13 @@ lbm_status lbm_set_bc(lbm_ctx *c, int face, int layers, double rho_a,
   if (layers > 0 && (!(rho_a > 0) || !(rho_b > 0) || !std::isfinite(rho_a) ||
                      !std::isfinite(rho_b)))
     return fail(c, LBM_EINVAL, "reservoir densities must be finite and > 0");
-  c->sp.res.layers[face] = layers;
-  c->sp.res.rho[face][0] = (float)rho_a;
-  c->sp.res.rho[face][1] = (float)rho_b;
+  hmcsc::Reservoirs &r = c->res_current;
+  r.layers[face] = layers;
+  r.rho[face][0] = layers > 0 ? (float)rho_a : 0.0f;
+  r.rho[face][1] = layers > 0 ? (float)rho_b : 0.0f;
   int any = 0;
-  for (int k = 0; k < kFaces; ++k) any |= c->sp.res.layers[k] > 0;
-  c->sp.res.any = any;
+  for (int k = 0; k < kFaces; ++k) any |= r.layers[k] > 0;
+  r.any = any;
   return LBM_OK;
 }
 
@@ -318,6 +344,8 @@ lbm_status lbm_collide_stream(lbm_ctx *c) {
     return fail(c, LBM_ESTATE, "lbm_density must precede lbm_collide_stream");
   cudaError_t e = hmcsc::launch_collide_stream(c->sp, c->ws, parity(c), c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "collide/stream kernel");
+  // The reservoirs in force now reset their layers at the end of this step.
+  c->sp.res = c->res_current;
   c->t += 1;
   return LBM_OK;
 }
@@ -370,7 +398,9 @@ lbm_status lbm_reduce(lbm_ctx *c, lbm_observables *out) {
   cudaError_t e = hmcsc::launch_density(c->sp, c->ws, parity(c), c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "density kernel");
   c->rho_at = c->t;
-  e = hmcsc::launch_reduce(c->sp, c->ws, c->stream);
+  hmcsc::StepParams obs = c->sp;
+  obs.res = c->res_current;
+  e = hmcsc::launch_reduce(obs, c->ws, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "reduce kernel");
   double r[kRedK];
   e = cudaMemcpyAsync(r, c->ws.red + (size_t)kRedBlocks * kRedK, sizeof r,
@@ -383,7 +413,7 @@ lbm_status lbm_reduce(lbm_ctx *c, lbm_observables *out) {
   out->sat1 = r[3] > 0.0 ? r[2] / r[3] : NAN;
   const long long ext[3] = {c->params.nx, c->params.ny, c->params.nz};
   for (int k = 0; k < kFaces; ++k) {
-    const int L = c->sp.res.layers[k];
+    const int L = c->res_current.layers[k];
     if (L == 0) {
       out->p_face[k] = NAN;
       continue;
@@ -443,13 +473,14 @@ lbm_status lbm_save(lbm_ctx *c, void *host_buf, size_t bytes) {
   CkptHeader h;
   memset(&h, 0, sizeof h);
   memcpy(h.magic, kMagic, 8);
-  h.version = 1;
+  h.version = 2;
   h.storage = c->params.storage;
   h.nx = c->params.nx;
   h.ny = c->params.ny;
   h.nz = c->params.nz;
   h.t = c->t;
   h.ntiles = c->sp.ntiles;
+  h.applied = c->sp.res;
   memcpy(host_buf, &h, sizeof h);
   cudaError_t e = cudaMemcpyAsync((char *)host_buf + sizeof h, c->ws.f,
                                   sizeof(float) * pop_floats(c),
@@ -464,7 +495,7 @@ lbm_status lbm_load(lbm_ctx *c, const void *host_buf, size_t bytes) {
     return fail(c, LBM_EINVAL, "checkpoint buffer too small");
   CkptHeader h;
   memcpy(&h, host_buf, sizeof h);
-  if (memcmp(h.magic, kMagic, 8) != 0 || h.version != 1)
+  if (memcmp(h.magic, kMagic, 8) != 0 || h.version != 2)
     return fail(c, LBM_EINVAL, "not a checkpoint of this library");
   if (h.nx != c->params.nx || h.ny != c->params.ny || h.nz != c->params.nz ||
       h.storage != c->params.storage || h.ntiles != c->sp.ntiles || h.t < 0)
@@ -478,6 +509,7 @@ lbm_status lbm_load(lbm_ctx *c, const void *host_buf, size_t bytes) {
   lbm_status st = sync_stream(c, "load");
   if (st) return st;
   c->t = h.t;
+  c->sp.res = h.applied;
   c->rho_at = -1;
   c->have_state = true;
   return LBM_OK;

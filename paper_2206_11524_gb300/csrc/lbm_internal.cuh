@@ -52,7 +52,8 @@ struct Reservoirs {
   int any;
 };
 
-// Per-launch constants.
+// Per-launch constants.  `res` lists the reservoirs whose reset ended the
+// previous step; kernels read a node inside one of them as its equilibrium.
 struct StepParams {
   int nx, ny, nz;
   int ntx;           // tiles along x: ceil(nx / 32)

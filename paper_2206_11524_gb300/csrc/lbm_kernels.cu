@@ -4,8 +4,15 @@
 //   k_density        rho_sigma(x) = sum_i f_i,sigma(x)                (Eq. A.4)
 //   k_collide_stream moments, Shan-Chen forces (Eqs. 3-5), equilibrium
 //                    velocity (Eq. 6), equilibrium (Eq. A.3), gray collision
-//                    with partial bounce-back (Eq. 1), in-place streaming and
-//                    the density reservoirs (Sec. 4)
+//                    with partial bounce-back (Eq. 1) and in-place streaming
+//
+// Density reservoirs (Sec. 4) reset their layers to the equilibrium at rest
+// after every step.  No kernel writes that reset: every reader of a node's
+// populations (both passes, the fields pass, the host read-back) takes
+// f_i = w_i rho_res for a node inside a reservoir, which is the state the
+// reset defines, and what neighbours streamed into its slots is never read.
+// StepParams::res holds the reservoirs that were in effect at the end of the
+// previous step.
 //
 // Populations live in 32-node x-tiles (see lbm_internal.cuh) and stream in
 // place with the AA pattern:
@@ -38,7 +45,11 @@ struct Geo {
   __device__ __forceinline__ int node(int dx, int dy, int dz) const {
     return tile(dx, dy, dz) * kTile + ln[dx + 1];
   }
-  __device__ __forceinline__ int xof(int dx) const { return tx[dx + 1] * kTile + ln[dx + 1]; }
+  // float offset of slot 0 of node x + (dx, dy, dz) in the population array
+  // (fits 32 bits: the host requires ntiles * 1216 < 2^32)
+  __device__ __forceinline__ unsigned pop_off(int dx, int dy, int dz) const {
+    return (unsigned)tile(dx, dy, dz) * (unsigned)kTileFloats + (unsigned)ln[dx + 1];
+  }
 };
 
 __device__ __forceinline__ Geo make_geo(const StepParams &p, int x, int y,
@@ -66,7 +77,7 @@ __device__ __forceinline__ Geo make_geo(const StepParams &p, int x, int y,
 // that node is at base[k * 32].
 __device__ __forceinline__ float *pop_base(float *f, const Geo &g, int dx,
                                            int dy, int dz) {
-  return f + (size_t)g.tile(dx, dy, dz) * kTileFloats + g.ln[dx + 1];
+  return f + g.pop_off(dx, dy, dz);
 }
 
 // The 19 populations of both components at the current time step.
@@ -162,33 +173,48 @@ __device__ __forceinline__ int res_face(const StepParams &p, int x, int y,
   return face;
 }
 
-// Does some node of the box [xlo,xhi] x [ylo,yhi] x [zlo,zhi] have a
-// (periodic) neighbour inside a reservoir?  Uniform over a block.
-__device__ __forceinline__ bool box_near_reservoir(const StepParams &p, int xlo,
-                                                   int xhi, int ylo, int yhi,
-                                                   int zlo, int zhi) {
+// rho_res of component s on face `face` (selects, no indexed parameter load).
+__device__ __forceinline__ float res_rho(const StepParams &p, int face, int s) {
+  float r = p.res.rho[0][s];
+#pragma unroll
+  for (int k = 1; k < kFaces; ++k) r = face == k ? p.res.rho[k][s] : r;
+  return r;
+}
+
+// Does the block's box [xlo,xhi] x [ylo,yhi] x [zlo,zhi] hold a node inside
+// a reservoir?  Uniform over the block, known before any load.
+__device__ __forceinline__ bool box_in_reservoir(const StepParams &p, int xlo,
+                                                 int xhi, int ylo, int yhi,
+                                                 int zlo, int zhi) {
   if (!p.res.any) return false;
   const int *L = p.res.layers;
-  const bool bx = (L[0] && (xlo <= L[0] || xhi >= p.nx - 1)) ||
-                  (L[1] && (xhi >= p.nx - 1 - L[1] || xlo == 0));
-  const bool by = (L[2] && (ylo <= L[2] || yhi >= p.ny - 1)) ||
-                  (L[3] && (yhi >= p.ny - 1 - L[3] || ylo == 0));
-  const bool bz = (L[4] && (zlo <= L[4] || zhi >= p.nz - 1)) ||
-                  (L[5] && (zhi >= p.nz - 1 - L[5] || zlo == 0));
-  return bx || by || bz;
+  return (L[0] && xlo < L[0]) || (L[1] && xhi >= p.nx - L[1]) ||
+         (L[2] && ylo < L[2]) || (L[3] && yhi >= p.ny - L[3]) ||
+         (L[4] && zlo < L[4]) || (L[5] && zhi >= p.nz - L[5]);
+}
+
+// A node inside a reservoir holds the prescribed equilibrium at rest.  Only
+// blocks whose box meets a reservoir (`maybe`, block-uniform) look.
+__device__ __forceinline__ void reservoir_state(const StepParams &p, bool maybe,
+                                                int x, int y, int z,
+                                                float (&v1)[kQ], float (&v2)[kQ]) {
+  if (!maybe) return;
+  const int face = res_face(p, x, y, z);
+  if (face >= 0) {
+    const float r1 = res_rho(p, face, 0), r2 = res_rho(p, face, 1);
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) {
+      v1[i] = wgt(i) * r1;
+      v2[i] = wgt(i) * r2;
+    }
+  }
 }
 
 // Store the post-collision population i of component s; it becomes
-// population i of node x + c_i at t + 1.  With RES, a destination inside a
-// reservoir receives the prescribed equilibrium w_i rho_res at rest instead
-// (the reset of Sec. 4, applied as the population arrives).
-template <int PARITY, bool RES>
-__device__ __forceinline__ void put(const StepParams &p, float *f,
-                                    const Geo &g, int s, int i, float val) {
-  if (RES) {
-    const int face = res_face(p, g.xof(cx(i)), g.yw[1 + cy(i)], g.zw[1 + cz(i)]);
-    if (face >= 0) val = wgt(i) * p.res.rho[face][s];
-  }
+// population i of node x + c_i at t + 1.
+template <int PARITY>
+__device__ __forceinline__ void put(float *f, const Geo &g, int s, int i,
+                                    float val) {
   if (PARITY == 0)
     pop_base(f, g, 0, 0, 0)[(s * kQ + opp(i)) * kTile] = val;
   else
@@ -200,7 +226,11 @@ __device__ __forceinline__ void put(const StepParams &p, float *f,
 // The rest population's equilibrium is taken as rho_s minus the other 18
 // (sum_i f^eq_i = rho_s holds exactly for Eq. A.3 on D3Q19), which keeps the
 // rounding of the float weights from leaking mass step after step.
-template <int PARITY, bool RES>
+//
+// The relaxation weight b = (1 - n_s) / tau is folded into the equilibrium:
+// B_i = b f^eq_i = (b w_i rho_s) [1 - 1.5 u.u + 4.5 (c_i.u)^2 +- 3 c_i.u],
+// so each population costs two fused multiply-adds on top of B_i.
+template <int PARITY>
 __device__ __forceinline__ void collide_put(const StepParams &p, float *f,
                                             const Geo &g, int s,
                                             const float (&v)[kQ], float rho_s,
@@ -208,31 +238,34 @@ __device__ __forceinline__ void collide_put(const StepParams &p, float *f,
   const float om = p.omega[s];
   const float a = (1.0f - nsx) * (1.0f - om);
   const float b = (1.0f - nsx) * om;
-  const float usq = 1.5f * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
-  float moving = 0.0f;
+  const float base = 1.0f - 1.5f * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+  const float br = b * rho_s;
+  const float br18 = br * (1.0f / 18.0f), br36 = br * (1.0f / 36.0f);
+  float moving = 0.0f;  // sum of B_i over the 18 moving directions
 #pragma unroll
   for (int i = 1; i <= 9; ++i) {
     const int j = i + 9;
     const float cu = cx(i) * u[0] + cy(i) * u[1] + cz(i) * u[2];
-    const float wr = wgt(i) * rho_s;
-    const float even = wr * (1.0f + 4.5f * cu * cu - usq);
-    const float odd = wr * 3.0f * cu;
-    const float fe_i = even + odd, fe_j = even - odd;
-    moving += fe_i + fe_j;
-    put<PARITY, RES>(p, f, g, s, i, a * v[i] + b * fe_i + nsx * v[j]);
-    put<PARITY, RES>(p, f, g, s, j, a * v[j] + b * fe_j + nsx * v[i]);
+    const float bw = wgt(i) == (1.0f / 18.0f) ? br18 : br36;
+    const float even = bw * fmaf(4.5f * cu, cu, base);
+    const float odd = (3.0f * bw) * cu;
+    const float B_i = even + odd, B_j = even - odd;
+    moving += B_i + B_j;
+    put<PARITY>(f, g, s, i, fmaf(a, v[i], fmaf(nsx, v[j], B_i)));
+    put<PARITY>(f, g, s, j, fmaf(a, v[j], fmaf(nsx, v[i], B_j)));
   }
-  const float fe_0 = rho_s - moving;
-  put<PARITY, RES>(p, f, g, s, 0, a * v[0] + b * fe_0 + nsx * v[0]);
+  const float B_0 = br - moving;  // b rho_s minus the moving ones: sum_i B_i = b rho_s
+  put<PARITY>(f, g, s, 0, fmaf(a + nsx, v[0], B_0));
 }
 
-template <int PARITY, bool RES>
+template <int PARITY>
 __device__ __forceinline__ void collide_body(const StepParams &p,
-                                             const Workspace &w, int x, int y,
-                                             int z) {
+                                             const Workspace &w, bool maybe_res,
+                                             int x, int y, int z) {
   const Geo g = make_geo(p, x, y, z);
   float f1[kQ], f2[kQ];
   load_pops<PARITY>(w.f, g, f1, f2);
+  reservoir_state(p, maybe_res, x, y, z, f1, f2);
   const float r1 = sum19(f1), r2 = sum19(f2);
   float j1[3], j2[3];
   first_moment(f1, j1);
@@ -253,8 +286,15 @@ __device__ __forceinline__ void collide_body(const StepParams &p,
   }
 
   const float nsx = w.ns[g.node(0, 0, 0)];
-  collide_put<PARITY, RES>(p, w.f, g, 0, f1, r1, u1, nsx);
-  collide_put<PARITY, RES>(p, w.f, g, 1, f2, r2, u2, nsx);
+  collide_put<PARITY>(p, w.f, g, 0, f1, r1, u1, nsx);
+  collide_put<PARITY>(p, w.f, g, 1, f2, r2, u2, nsx);
+}
+
+template <int BZ>
+__device__ __forceinline__ bool block_in_reservoir(const StepParams &p) {
+  const int xlo = blockIdx.x * kTile, ylo = blockIdx.y * kBY, zlo = blockIdx.z * BZ;
+  return box_in_reservoir(p, xlo, min(xlo + kTile, p.nx) - 1, ylo,
+                          min(ylo + kBY, p.ny) - 1, zlo, min(zlo + BZ, p.nz) - 1);
 }
 
 __device__ __forceinline__ void block_coords(int &x, int &y, int &z) {
@@ -267,36 +307,42 @@ template <int PARITY>
 __global__ void __launch_bounds__(kThreads) k_density(StepParams p, Workspace w) {
   int x, y, z;
   block_coords(x, y, z);
+  const bool maybe_res = block_in_reservoir<kBZ>(p);
   if (x >= p.nx || y >= p.ny || z >= p.nz) return;
   const Geo g = make_geo(p, x, y, z);
   float v1[kQ], v2[kQ];
   load_pops<PARITY>(w.f, g, v1, v2);
+  reservoir_state(p, maybe_res, x, y, z, v1, v2);
   w.rho[g.node(0, 0, 0)] = make_float2(sum19(v1), sum19(v2));
 }
 
 // Register budget per parity: the even step keeps one tile pointer and fits
-// 80 registers (3 blocks / SM); the odd step keeps one pointer per neighbour
-// offset and gets 128 (2 blocks / SM) so that nothing spills.
+// 80 registers (3 blocks / SM); the odd step keeps one offset per neighbour
+// and gets more so that nothing spills.
 #ifndef HMCSC_MINB_EVEN
 #define HMCSC_MINB_EVEN 3
 #endif
+#ifndef HMCSC_ODD_BZ
+#define HMCSC_ODD_BZ 1
+#endif
 #ifndef HMCSC_MINB_ODD
-#define HMCSC_MINB_ODD 2
+#define HMCSC_MINB_ODD 5
 #endif
 template <int PARITY>
-__global__ void __launch_bounds__(kThreads, PARITY == 0 ? HMCSC_MINB_EVEN : HMCSC_MINB_ODD)
+struct CollideShape {
+  static constexpr int BZ = PARITY == 0 ? kBZ : HMCSC_ODD_BZ;
+  static constexpr int threads = kTile * kBY * BZ;
+  static constexpr int minb = PARITY == 0 ? HMCSC_MINB_EVEN : HMCSC_MINB_ODD;
+};
+template <int PARITY>
+__global__ void __launch_bounds__(CollideShape<PARITY>::threads, CollideShape<PARITY>::minb)
     k_collide_stream(StepParams p, Workspace w) {
-  int x, y, z;
-  block_coords(x, y, z);
-  const int xlo = blockIdx.x * kTile, ylo = blockIdx.y * kBY, zlo = blockIdx.z * kBZ;
-  const bool res = box_near_reservoir(p, xlo, min(xlo + kTile - 1, p.nx - 1), ylo,
-                                      min(ylo + kBY - 1, p.ny - 1), zlo,
-                                      min(zlo + kBZ - 1, p.nz - 1));
+  const int x = blockIdx.x * kTile + threadIdx.x;
+  const int y = blockIdx.y * kBY + threadIdx.y;
+  const int z = blockIdx.z * CollideShape<PARITY>::BZ + threadIdx.z;
+  const bool maybe_res = block_in_reservoir<CollideShape<PARITY>::BZ>(p);
   if (x >= p.nx || y >= p.ny || z >= p.nz) return;
-  if (res)
-    collide_body<PARITY, true>(p, w, x, y, z);
-  else
-    collide_body<PARITY, false>(p, w, x, y, z);
+  collide_body<PARITY>(p, w, maybe_res, x, y, z);
 }
 
 // Macroscopic fields of the current state into the linear staging planes:
@@ -305,10 +351,12 @@ template <int PARITY>
 __global__ void __launch_bounds__(kThreads) k_fields(StepParams p, Workspace w) {
   int x, y, z;
   block_coords(x, y, z);
+  const bool maybe_res = block_in_reservoir<kBZ>(p);
   if (x >= p.nx || y >= p.ny || z >= p.nz) return;
   const Geo g = make_geo(p, x, y, z);
   float f1[kQ], f2[kQ];
   load_pops<PARITY>(w.f, g, f1, f2);
+  reservoir_state(p, maybe_res, x, y, z, f1, f2);
   const float r1 = sum19(f1), r2 = sum19(f2);
   float j1[3], j2[3];
   first_moment(f1, j1);
@@ -500,11 +548,15 @@ cudaError_t launch_density(const StepParams &p, const Workspace &w, int parity,
 
 cudaError_t launch_collide_stream(const StepParams &p, const Workspace &w,
                                   int parity, cudaStream_t s) {
-  const dim3 block(kTile, kBY, kBZ);
-  if (parity == 0)
-    k_collide_stream<0><<<node_grid(p), block, 0, s>>>(p, w);
-  else
-    k_collide_stream<1><<<node_grid(p), block, 0, s>>>(p, w);
+  if (parity == 0) {
+    constexpr int BZ = CollideShape<0>::BZ;
+    const dim3 grid(p.ntx, (p.ny + kBY - 1) / kBY, (p.nz + BZ - 1) / BZ);
+    k_collide_stream<0><<<grid, dim3(kTile, kBY, BZ), 0, s>>>(p, w);
+  } else {
+    constexpr int BZ = CollideShape<1>::BZ;
+    const dim3 grid(p.ntx, (p.ny + kBY - 1) / kBY, (p.nz + BZ - 1) / BZ);
+    k_collide_stream<1><<<grid, dim3(kTile, kBY, BZ), 0, s>>>(p, w);
+  }
   return cudaGetLastError();
 }
 

@@ -118,6 +118,37 @@ def test_reservoirs_and_corners_match():
     assert all(math.isnan(v) for v in og["p_face"][3:])
 
 
+def test_inlet_ramp_between_steps():
+    """An inlet reservoir whose density is raised between steps (the ramp of
+    Sec. 4) and a face added mid-run: GPU and oracle apply each change at the
+    end of the next step."""
+    shape = (4, 6, 20)
+    ns, gads = synth.random_geometry(shape, 91)
+    res = {0: (4, 1.00, 0.02), 1: (4, 0.02, 0.99)}
+    g, r = pair(shape, ns=ns, gads=gads, res=res)
+    ra = np.where(np.arange(20) < 10, 0.99, 0.02) * np.ones(shape)
+    g.init_equilibrium(ra, 1.0 - ra)
+    r.init_equilibrium(w64(ra), w64(1.0 - ra))
+    for k in range(6):
+        g.step(1)
+        r.step(1)
+        if k in (1, 3):
+            res[0] = (4, 1.00 + 0.02 * (k + 1), 0.02)
+            g.set_bc(0, *res[0])
+            r.set_reservoirs(res)
+        if k == 4:
+            res[3] = (1, 0.5, 0.5)
+            g.set_bc(3, *res[3])
+            r.set_reservoirs(res)
+        assert np.abs(g.populations() - r.f).max() <= 2e-6 * np.abs(r.f).max(), k
+    ck = g.save()
+    g.step(3)
+    want = g.populations()
+    g.load(ck)
+    g.step(3)
+    assert np.array_equal(g.populations(), want)
+
+
 def test_gray_slab_500_steps():
     """The 32 x 16 x 16 gray-slab workload (n_s = 0.5 at x = 12..19, fluid 1
     for x < 16, majority 1.0 / minority 0.03, tau = 1, G = 1.75, F along x)
