@@ -309,6 +309,22 @@ def test_invalid_arguments_are_rejected():
     lbm.lbm_sync(g.ctx, 10.0)
 
 
+def test_sync_watchdog_times_out_and_recovers():
+    """lbm_sync returns ETIMEOUT when the queued work outlasts the limit and
+    leaves the context usable; a later sync with room succeeds."""
+    case = synth.electrode((128, 128, 128))
+    g = lbm.Lattice(128, 128, 128, tau=case.tau, G=case.G)
+    g.set_geometry(case.ns, case.gads2)
+    g.init_equilibrium(case.rho_a, case.rho_b)
+    lbm.lbm_step(g.ctx, 200)
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.lbm_sync(g.ctx, 1e-6)
+    assert e.value.status == lbm.LBM_ETIMEOUT
+    lbm.lbm_sync(g.ctx, 60.0)
+    assert g.t == 200 and g.observables()["nonfinite"] == 0
+    g.close()
+
+
 def _sampled_reference(case, nodes, steps):
     """Oracle value of f at `nodes` after `steps` steps, each computed on a
     periodic box of half-width 2*steps+1 cut around the node: a node's state
