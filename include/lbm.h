@@ -55,7 +55,14 @@ typedef enum {
 } lbm_status;
 
 typedef enum {
-  LBM_STORAGE_F32 = 0 /* populations stored as float32 */
+  LBM_STORAGE_F32 = 0,         /* populations stored as float32             */
+  LBM_STORAGE_F16_OFFSET = 1,  /* f_i - w_i rho0_sigma stored as IEEE half   */
+  LBM_STORAGE_BF16_OFFSET = 2, /* f_i - w_i rho0_sigma stored as bfloat16    */
+  LBM_STORAGE_F16_LOCAL = 3,   /* f_i - w_i rho_sigma(x - c_i, t - 1) as half:
+                                  the offset from the rest equilibrium of the
+                                  node that wrote the population, at the step
+                                  it wrote it (two density buffers)          */
+  LBM_STORAGE_BF16_LOCAL = 4   /* the same, stored as bfloat16               */
 } lbm_storage;
 
 /* Model parameters (names of Table 1). */
@@ -65,6 +72,10 @@ typedef struct {
   double tau[2];     /* relaxation times tau_1, tau_2 > 1/2         (Eq. 1) */
   double G;          /* G_inter,12 = G_inter,21                     (Eq. 3) */
   double F_ext[3];   /* body force on the mixture, split by Eq. 5           */
+  double rho0[2];    /* offset reference per component for the 16-bit
+                        storages (populations are kept as f_i - w_i rho0);
+                        ignored for LBM_STORAGE_F32.  All arithmetic is
+                        float32 whatever the storage.                       */
 } lbm_params;
 
 /* Observables of the current state (Sec. 4, Eqs. 18-19, Eq. A.6). */
@@ -82,8 +93,9 @@ typedef struct {
 typedef struct lbm_ctx lbm_ctx;
 
 /* Bytes of device workspace a context with these parameters needs
- * (populations 2 x 19 x N floats, densities, geometry, output staging and
- * reduction scratch).  Returns 0 if the parameters are invalid. */
+ * (populations 2 x 19 x N values of the storage type, densities, geometry,
+ * output staging and reduction scratch).  Returns 0 if the parameters are
+ * invalid. */
 LBM_API size_t lbm_workspace_bytes(const lbm_params *params);
 
 /* Create a context.  d_workspace: device pointer, 256-byte aligned, at least

@@ -23,6 +23,8 @@ using hmcsc::kRedK;
 struct lbm_ctx {
   lbm_params params;
   hmcsc::StepParams sp;   // sp.res: reservoirs applied at the end of the last step
+  float2 *rho_buf[2];     // *_LOCAL storages: the two density buffers
+  int enc;                // index of rho_buf holding the encoding densities
   hmcsc::Reservoirs res_current;  // reservoirs set by lbm_set_bc (next steps)
   hmcsc::Workspace ws;
   cudaStream_t stream;
@@ -63,7 +65,10 @@ bool params_valid(const lbm_params *p, const char **why) {
       tl.ntiles * (long long)hmcsc::kTileFloats > 4294967295LL) {
     *why = "lattice too large for 32-node x-tiles"; return false;
   }
-  if (p->storage != LBM_STORAGE_F32) { *why = "unsupported storage"; return false; }
+  if (p->storage < LBM_STORAGE_F32 || p->storage > LBM_STORAGE_BF16_LOCAL) {
+    *why = "unsupported storage"; return false;
+  }
+  if (!std::isfinite(p->rho0[0]) || !std::isfinite(p->rho0[1])) { *why = "rho0 must be finite"; return false; }
   for (int s = 0; s < 2; ++s)
     if (!(p->tau[s] > 0.5) || !std::isfinite(p->tau[s])) { *why = "tau must be finite and > 1/2"; return false; }
   if (!std::isfinite(p->G)) { *why = "G must be finite"; return false; }
@@ -74,6 +79,52 @@ bool params_valid(const lbm_params *p, const char **why) {
 
 size_t lin_stride(const lbm_ctx *c) { return (size_t)c->sp.nlin; }
 size_t pop_floats(const lbm_ctx *c) { return (size_t)c->sp.ntiles * hmcsc::kTileFloats; }
+size_t pop_bytes(const lbm_ctx *c) {
+  return pop_floats(c) * (size_t)hmcsc::storage_bytes(c->sp.storage);
+}
+
+// Host-side encode / decode of one population in the context's storage
+// with the reference w_i rho_ref already formed (the same float operations
+// the kernels use: subtract, round to nearest into half / bfloat16; decode
+// by adding the reference back).
+void encode(int storage, void *dst, size_t idx, float f, float ref) {
+  if (storage == hmcsc::kF16 || storage == hmcsc::kF16L)
+    static_cast<__half *>(dst)[idx] = __float2half_rn((f - ref) * hmcsc::kHalfScale);
+  else if (storage == hmcsc::kBF16 || storage == hmcsc::kBF16L)
+    static_cast<__nv_bfloat16 *>(dst)[idx] = __float2bfloat16_rn(f - ref);
+  else
+    static_cast<float *>(dst)[idx] = f;
+}
+float decode(int storage, const void *src, size_t idx, float ref) {
+  if (storage == hmcsc::kF16 || storage == hmcsc::kF16L)
+    return ref + __half2float(static_cast<const __half *>(src)[idx]) * hmcsc::kHalfUnscale;
+  if (storage == hmcsc::kBF16 || storage == hmcsc::kBF16L)
+    return ref + __bfloat162float(static_cast<const __nv_bfloat16 *>(src)[idx]);
+  return static_cast<const float *>(src)[idx];
+}
+
+// Tiled node index of (x, y, z).
+size_t tiled_node(const lbm_ctx *c, long long x, long long y, long long z) {
+  const long long t = x / hmcsc::kTile + c->sp.ntx * (y + (long long)c->params.ny * z);
+  return (size_t)t * hmcsc::kTile + (size_t)(x % hmcsc::kTile);
+}
+
+// Point the workspace's density views at the buffers of the current state.
+void set_density_views(lbm_ctx *c) {
+  if (!hmcsc::storage_local(c->sp.storage)) return;
+  c->ws.rho_enc = c->rho_buf[c->enc];
+  c->ws.rho = c->rho_buf[1 - c->enc];
+}
+
+// Reference of population i (component s) of node (x,y,z) for decoding or
+// encoding it as stored: *_LOCAL uses the node's own previous density in
+// rho_enc (host copy, tiled float2), *_OFFSET the constant table.
+float stored_ref(const lbm_ctx *c, const float *rho_enc_host, int s, int i,
+                 int x, int y, int z) {
+  if (hmcsc::storage_local(c->sp.storage))
+    return hmcsc::wgt(i) * rho_enc_host[2 * tiled_node(c, x, y, z) + s];
+  return c->sp.ref[s][hmcsc::wclass(i)];
+}
 
 // Offset (in floats) of slot k of node (x, y, z) in the tiled population
 // layout.
@@ -128,8 +179,8 @@ extern "C" {
 size_t lbm_workspace_bytes(const lbm_params *params) {
   const char *why = nullptr;
   if (!params_valid(params, &why)) return 0;
-  return hmcsc::workspace_bytes(params->nx, params->ny, params->nz, nullptr,
-                                nullptr);
+  return hmcsc::workspace_bytes(params->nx, params->ny, params->nz,
+                                params->storage, nullptr, nullptr);
 }
 
 lbm_status lbm_create(const lbm_params *params, void *d_workspace,
@@ -140,15 +191,15 @@ lbm_status lbm_create(const lbm_params *params, void *d_workspace,
   const char *why = nullptr;
   if (!params_valid(params, &why)) return LBM_EINVAL;
   if (!d_workspace || ((uintptr_t)d_workspace & 255u)) return LBM_EINVAL;
-  const size_t need = hmcsc::workspace_bytes(params->nx, params->ny,
-                                             params->nz, nullptr, nullptr);
+  const size_t need = hmcsc::workspace_bytes(params->nx, params->ny, params->nz,
+                                             params->storage, nullptr, nullptr);
   if (workspace_bytes < need) return LBM_ENOMEM;
   lbm_ctx *c = new lbm_ctx();
   c->params = *params;
   c->stream = (cudaStream_t)cuda_stream;
   c->N = (long long)params->nx * params->ny * params->nz;
-  hmcsc::workspace_bytes(params->nx, params->ny, params->nz, &c->ws,
-                         (char *)d_workspace);
+  hmcsc::workspace_bytes(params->nx, params->ny, params->nz, params->storage,
+                         &c->ws, (char *)d_workspace);
   hmcsc::StepParams &sp = c->sp;
   sp.nx = params->nx;
   sp.ny = params->ny;
@@ -162,9 +213,20 @@ lbm_status lbm_create(const lbm_params *params, void *d_workspace,
     sp.omega[s] = (float)(1.0 / params->tau[s]);
   }
   sp.G = (float)params->G;
+  sp.storage = params->storage;
+  for (int s = 0; s < 2; ++s) {
+    const float r0 = (float)params->rho0[s];
+    sp.ref[s][0] = hmcsc::wgt(0) * r0;
+    sp.ref[s][1] = hmcsc::wgt(1) * r0;
+    sp.ref[s][2] = hmcsc::wgt(4) * r0;
+  }
   for (int d = 0; d < 3; ++d) sp.F[d] = (float)params->F_ext[d];
   memset(&sp.res, 0, sizeof sp.res);
   memset(&c->res_current, 0, sizeof c->res_current);
+  c->rho_buf[0] = c->ws.rho;
+  c->rho_buf[1] = c->ws.rho_enc;
+  c->enc = 1;
+  set_density_views(c);
   c->t = 0;
   c->rho_at = -1;
   c->have_geometry = false;
@@ -251,17 +313,40 @@ lbm_status lbm_set_populations(lbm_ctx *c, const float *f) {
       }
       if (!(r > 0.0f)) return fail(c, LBM_EINVAL, "component %d density <= 0 at node %lld", s, n);
     }
-  std::vector<float> tiled(pop_floats(c), 0.0f);
+  std::vector<char> tiled(pop_bytes(c), 0);
   const int nx = c->params.nx, ny = c->params.ny, nz = c->params.nz;
-  for (int k = 0; k < 2 * kQ; ++k)
+  const bool local = hmcsc::storage_local(c->sp.storage);
+  // *_LOCAL: the given state is offset from its own nodes' densities
+  // (summed in direction order, as the kernels do).
+  std::vector<float> rho_enc(local ? 2 * (size_t)c->sp.ntiles * hmcsc::kTile : 0, 0.0f);
+  if (local)
     for (int z = 0; z < nz; ++z)
       for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x)
-          tiled[pop_offset(c, k, x, y, z)] =
-              f[(size_t)k * N + x + (size_t)nx * (y + (size_t)ny * z)];
-  cudaError_t e = cudaMemcpyAsync(c->ws.f, tiled.data(), tiled.size() * sizeof(float),
+          for (int sg = 0; sg < 2; ++sg) {
+            float r = 0.0f;
+            for (int i = 0; i < kQ; ++i)
+              r += f[((size_t)sg * kQ + i) * N + x + (size_t)nx * (y + (size_t)ny * z)];
+            rho_enc[2 * tiled_node(c, x, y, z) + sg] = r;
+          }
+  for (int sg = 0; sg < 2; ++sg)
+    for (int i = 0; i < kQ; ++i)
+      for (int z = 0; z < nz; ++z)
+        for (int y = 0; y < ny; ++y)
+          for (int x = 0; x < nx; ++x) {
+            const int k = sg * kQ + i;
+            encode(c->sp.storage, tiled.data(), pop_offset(c, k, x, y, z),
+                   f[(size_t)k * N + x + (size_t)nx * (y + (size_t)ny * z)],
+                   stored_ref(c, rho_enc.data(), sg, i, x, y, z));
+          }
+  cudaError_t e = cudaMemcpyAsync(c->ws.f, tiled.data(), tiled.size(),
                                   cudaMemcpyHostToDevice, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "host-to-device copy");
+  if (local) {
+    e = cudaMemcpyAsync(c->ws.rho_enc, rho_enc.data(), rho_enc.size() * sizeof(float),
+                        cudaMemcpyHostToDevice, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "host-to-device copy");
+  }
   lbm_status st = sync_stream(c, "set_populations");
   if (st) return st;
   memset(&c->sp.res, 0, sizeof c->sp.res);
@@ -276,10 +361,17 @@ lbm_status lbm_get_populations(lbm_ctx *c, float *f) {
   if (!f) return fail(c, LBM_EINVAL, "f is NULL");
   if (!c->have_state) return fail(c, LBM_ESTATE, "no state set");
   const long long N = c->N;
-  std::vector<float> raw(pop_floats(c));
-  cudaError_t e = cudaMemcpyAsync(raw.data(), c->ws.f, raw.size() * sizeof(float),
+  std::vector<char> raw(pop_bytes(c));
+  cudaError_t e = cudaMemcpyAsync(raw.data(), c->ws.f, raw.size(),
                                   cudaMemcpyDeviceToHost, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "device-to-host copy");
+  const bool local = hmcsc::storage_local(c->sp.storage);
+  std::vector<float> rho_enc(local ? 2 * (size_t)c->sp.ntiles * hmcsc::kTile : 0);
+  if (local) {
+    e = cudaMemcpyAsync(rho_enc.data(), c->ws.rho_enc, rho_enc.size() * sizeof(float),
+                        cudaMemcpyDeviceToHost, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "device-to-host copy");
+  }
   lbm_status st = sync_stream(c, "get_populations");
   if (st) return st;
   const int nx = c->params.nx, ny = c->params.ny, nz = c->params.nz;
@@ -291,13 +383,16 @@ lbm_status lbm_get_populations(lbm_ctx *c, float *f) {
             const long long n = x + (long long)nx * (y + (long long)ny * z);
             float v;
             if (parity(c) == 0) {
-              v = raw[pop_offset(c, s * kQ + i, x, y, z)];
+              v = decode(c->sp.storage, raw.data(), pop_offset(c, s * kQ + i, x, y, z),
+                         stored_ref(c, rho_enc.data(), s, i, x, y, z));
             } else {
               // population i of node n sits in slot opp(i) of node n - c_i
               const int xs = (x - hmcsc::cx(i) + nx) % nx;
               const int ys = (y - hmcsc::cy(i) + ny) % ny;
               const int zs = (z - hmcsc::cz(i) + nz) % nz;
-              v = raw[pop_offset(c, s * kQ + hmcsc::opp(i), xs, ys, zs)];
+              v = decode(c->sp.storage, raw.data(),
+                         pop_offset(c, s * kQ + hmcsc::opp(i), xs, ys, zs),
+                         stored_ref(c, rho_enc.data(), s, i, x, y, z));
             }
             if (c->sp.res.any) {
               // a node inside a reservoir holds w_i rho_res (see the kernels)
@@ -346,6 +441,11 @@ lbm_status lbm_collide_stream(lbm_ctx *c) {
   if (e != cudaSuccess) return cuda_fail(c, e, "collide/stream kernel");
   // The reservoirs in force now reset their layers at the end of this step.
   c->sp.res = c->res_current;
+  // *_LOCAL: the densities of this step are the encoding densities now.
+  if (hmcsc::storage_local(c->sp.storage)) {
+    c->enc = 1 - c->enc;
+    set_density_views(c);
+  }
   c->t += 1;
   return LBM_OK;
 }
@@ -460,9 +560,16 @@ lbm_status lbm_sync(lbm_ctx *c, double timeout_s) {
   return st;
 }
 
+// Bytes of the encoding densities a *_LOCAL checkpoint carries.
+size_t enc_bytes(const lbm_ctx *c) {
+  return hmcsc::storage_local(c->sp.storage)
+             ? sizeof(float2) * (size_t)c->sp.ntiles * hmcsc::kTile
+             : 0;
+}
+
 size_t lbm_checkpoint_bytes(const lbm_ctx *c) {
   if (!c) return 0;
-  return sizeof(CkptHeader) + sizeof(float) * pop_floats(c);
+  return sizeof(CkptHeader) + pop_bytes(c) + enc_bytes(c);
 }
 
 lbm_status lbm_save(lbm_ctx *c, void *host_buf, size_t bytes) {
@@ -483,9 +590,14 @@ lbm_status lbm_save(lbm_ctx *c, void *host_buf, size_t bytes) {
   h.applied = c->sp.res;
   memcpy(host_buf, &h, sizeof h);
   cudaError_t e = cudaMemcpyAsync((char *)host_buf + sizeof h, c->ws.f,
-                                  sizeof(float) * pop_floats(c),
+                                  pop_bytes(c),
                                   cudaMemcpyDeviceToHost, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "device-to-host copy");
+  if (enc_bytes(c)) {
+    e = cudaMemcpyAsync((char *)host_buf + sizeof h + pop_bytes(c), c->ws.rho_enc,
+                        enc_bytes(c), cudaMemcpyDeviceToHost, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "device-to-host copy");
+  }
   return sync_stream(c, "save");
 }
 
@@ -503,9 +615,14 @@ lbm_status lbm_load(lbm_ctx *c, const void *host_buf, size_t bytes) {
   if (bytes < lbm_checkpoint_bytes(c))
     return fail(c, LBM_EINVAL, "checkpoint truncated");
   cudaError_t e = cudaMemcpyAsync(c->ws.f, (const char *)host_buf + sizeof h,
-                                  sizeof(float) * pop_floats(c),
+                                  pop_bytes(c),
                                   cudaMemcpyHostToDevice, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "host-to-device copy");
+  if (enc_bytes(c)) {
+    e = cudaMemcpyAsync(c->ws.rho_enc, (const char *)host_buf + sizeof h + pop_bytes(c),
+                        enc_bytes(c), cudaMemcpyHostToDevice, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "host-to-device copy");
+  }
   lbm_status st = sync_stream(c, "load");
   if (st) return st;
   c->t = h.t;

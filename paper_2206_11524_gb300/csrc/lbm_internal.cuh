@@ -2,6 +2,8 @@
 // launchers of the HMCSC D3Q19 library (sm_103a).  Internal to the library.
 #pragma once
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stddef.h>
 #include <stdint.h>
@@ -17,7 +19,52 @@ constexpr int kFaces = 6;
 // A warp's access to one slot of its tile is one aligned 128-byte line, and
 // every slot of a tile sits at a fixed offset from the tile's base.
 constexpr int kTile = 32;
-constexpr int kTileFloats = 2 * kQ * kTile;
+constexpr int kTileFloats = 2 * kQ * kTile;  // populations per tile
+
+// Population storage.  F32 stores f_i.  The 16-bit formats store an offset
+// f_i - w_i rho_ref and decode to float32 for all arithmetic:
+//   *_OFFSET: rho_ref = rho0_sigma, one constant per component;
+//   *_LOCAL:  rho_ref = rho_sigma(y, t) for a population of node y at time
+//             t + 1, i.e. the owner's own density one step earlier, so the
+//             stored value is the deviation from that node's previous rest
+//             equilibrium and keeps 16-bit precision relative to each
+//             component's own local density.  A reader decodes all of its
+//             populations with its own previous density; a writer encodes
+//             with the destination's current density, which the force
+//             stencil loads anyway.
+// Half offsets are stored scaled by 2^14 (exact), which keeps offsets down
+// to ~1e-8 out of the half subnormal range; bfloat16 needs no scale.
+enum StorageKind { kF32 = 0, kF16 = 1, kBF16 = 2, kF16L = 3, kBF16L = 4 };
+__host__ __device__ constexpr int storage_bytes(int st) { return st == kF32 ? 4 : 2; }
+__host__ __device__ constexpr bool storage_local(int st) { return st == kF16L || st == kBF16L; }
+// weight class of direction i: 0 rest, 1 axis, 2 diagonal
+__host__ __device__ constexpr int wclass(int i) {
+  return i == 0 ? 0 : ((i <= 3 || (i >= 10 && i <= 12)) ? 1 : 2);
+}
+
+template <int ST> struct Codec;
+template <> struct Codec<kF32> {
+  using T = float;
+  static __device__ __forceinline__ float dec(T v, float) { return v; }
+  static __device__ __forceinline__ T enc(float f, float) { return f; }
+};
+constexpr float kHalfScale = 16384.0f, kHalfUnscale = 1.0f / 16384.0f;
+template <> struct Codec<kF16> {
+  using T = __half;
+  static __device__ __forceinline__ float dec(T v, float ref) {
+    return ref + __half2float(v) * kHalfUnscale;
+  }
+  static __device__ __forceinline__ T enc(float f, float ref) {
+    return __float2half_rn((f - ref) * kHalfScale);
+  }
+};
+template <> struct Codec<kBF16> {
+  using T = __nv_bfloat16;
+  static __device__ __forceinline__ float dec(T v, float ref) { return ref + __bfloat162float(v); }
+  static __device__ __forceinline__ T enc(float f, float ref) { return __float2bfloat16_rn(f - ref); }
+};
+template <> struct Codec<kF16L> : Codec<kF16> {};
+template <> struct Codec<kBF16L> : Codec<kBF16> {};
 
 // D3Q19 velocity set in the order of Eq. A.8: direction i + 9 is the
 // opposite of direction i (i = 1..9).
@@ -63,14 +110,19 @@ struct StepParams {
   float tau[2];
   float G;
   float F[3];
+  float ref[2][3];   // *_OFFSET storages: w_class * rho0_sigma (float product)
+  int storage;       // StorageKind
   Reservoirs res;
 };
 
 // Device workspace carved out of the caller's buffer.  Tiled arrays are
 // indexed by tiled node index t * 32 + x % 32 (padding lanes x >= nx unused).
 struct Workspace {
-  float *f;          // [ntiles][38][32] populations, AA layout at parity t & 1
+  void *f;           // [ntiles][38][32] populations (storage type), AA layout at parity t & 1
   float2 *rho;       // [ntiles * 32] (rho_1, rho_2) of the current time step
+  float2 *rho_enc;   // [ntiles * 32] *_LOCAL storages: each node's density of
+                     // the previous step, which its stored populations are
+                     // offset from
   float *ns;         // [ntiles * 32] bounce-back fraction n_s
   float *ads;        // [ntiles * 32] a = G_ads,2 * n_s (adhesion stencil source)
   float *stage;      // [6][nlin] linear (x fastest) staging for host transfers
@@ -93,8 +145,8 @@ __host__ __device__ inline Tiling tiling(long long nx, long long ny, long long n
   return t;
 }
 
-size_t workspace_bytes(long long nx, long long ny, long long nz, Workspace *out,
-                       char *base);
+size_t workspace_bytes(long long nx, long long ny, long long nz, int storage,
+                       Workspace *out, char *base);
 
 // Kernel launchers (return the launch error).
 cudaError_t launch_init_equilibrium(const StepParams &p, const Workspace &w,

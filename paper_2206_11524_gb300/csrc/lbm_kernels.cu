@@ -75,29 +75,50 @@ __device__ __forceinline__ Geo make_geo(const StepParams &p, int x, int y,
 
 // Lane-adjusted base of the tile holding node x + (dx, dy, dz): slot k of
 // that node is at base[k * 32].
-__device__ __forceinline__ float *pop_base(float *f, const Geo &g, int dx,
-                                           int dy, int dz) {
+template <typename T>
+__device__ __forceinline__ T *pop_base(T *f, const Geo &g, int dx, int dy,
+                                       int dz) {
   return f + g.pop_off(dx, dy, dz);
 }
 
-// The 19 populations of both components at the current time step.
-template <int PARITY>
-__device__ __forceinline__ void load_pops(float *f, const Geo &g,
-                                          float (&v1)[kQ], float (&v2)[kQ]) {
+// Decode references of population i of node x (both components): w_i times
+// the node's own previous density (*_LOCAL) or the constants (*_OFFSET).
+// The product is rounded on its own (no contraction) so that the host
+// read-back decodes identically.
+template <int ST>
+__device__ __forceinline__ float2 dec_ref(const StepParams &p, float2 own_prev,
+                                          int i) {
+  if (storage_local(ST))
+    return make_float2(__fmul_rn(wgt(i), own_prev.x), __fmul_rn(wgt(i), own_prev.y));
+  return make_float2(p.ref[0][wclass(i)], p.ref[1][wclass(i)]);
+}
+
+// The 19 populations of both components at the current time step, decoded
+// to float32.
+template <int PARITY, int ST>
+__device__ __forceinline__ void load_pops(const StepParams &p, const Workspace &w,
+                                          const Geo &g, float (&v1)[kQ],
+                                          float (&v2)[kQ]) {
+  using C = Codec<ST>;
+  typename C::T *f = static_cast<typename C::T *>(w.f);
+  const float2 own_prev = storage_local(ST) ? __ldg(&w.rho_enc[g.node(0, 0, 0)])
+                                            : make_float2(0.f, 0.f);
   if (PARITY == 0) {
-    const float *b = pop_base(f, g, 0, 0, 0);
+    const typename C::T *b = pop_base(f, g, 0, 0, 0);
 #pragma unroll
     for (int i = 0; i < kQ; ++i) {
-      v1[i] = b[i * kTile];
-      v2[i] = b[(kQ + i) * kTile];
+      const float2 r = dec_ref<ST>(p, own_prev, i);
+      v1[i] = C::dec(b[i * kTile], r.x);
+      v2[i] = C::dec(b[(kQ + i) * kTile], r.y);
     }
   } else {
 #pragma unroll
     for (int i = 0; i < kQ; ++i) {
       // population i of node x sits in slot opp(i) of node x - c_i
-      const float *b = pop_base(f, g, -cx(i), -cy(i), -cz(i));
-      v1[i] = b[opp(i) * kTile];
-      v2[i] = b[(kQ + opp(i)) * kTile];
+      const typename C::T *b = pop_base(f, g, -cx(i), -cy(i), -cz(i));
+      const float2 r = dec_ref<ST>(p, own_prev, i);
+      v1[i] = C::dec(b[opp(i) * kTile], r.x);
+      v2[i] = C::dec(b[(kQ + opp(i)) * kTile], r.y);
     }
   }
 }
@@ -212,13 +233,38 @@ __device__ __forceinline__ void reservoir_state(const StepParams &p, bool maybe,
 
 // Store the post-collision population i of component s; it becomes
 // population i of node x + c_i at t + 1.
-template <int PARITY>
-__device__ __forceinline__ void put(float *f, const Geo &g, int s, int i,
-                                    float val) {
+// A read-only load the compiler may neither merge with an earlier load of
+// the same address nor hoist: keeps a value that is needed late from
+// occupying a register from the start of the kernel.
+__device__ __forceinline__ float2 ld_late(const float2 *ptr) {
+  float2 v;
+  asm volatile("ld.global.nc.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(ptr));
+  return v;
+}
+
+// Encoding reference: w_i times the destination x + c_i's density at this
+// step (*_LOCAL; rho_s for the rest population, the densities pass's value
+// otherwise), or the constant w_i rho0_sigma (*_OFFSET).
+template <int PARITY, int ST>
+__device__ __forceinline__ void put(const StepParams &p, const Workspace &w,
+                                    const Geo &g, int s, int i, float val,
+                                    float rho_s) {
+  using C = Codec<ST>;
+  typename C::T *f = static_cast<typename C::T *>(w.f);
+  float ref = p.ref[s][wclass(i)];
+  if (storage_local(ST)) {
+    float rd = rho_s;
+    if (i != 0) {
+      const float2 r = ld_late(&w.rho[g.node(cx(i), cy(i), cz(i))]);
+      rd = s == 0 ? r.x : r.y;
+    }
+    ref = __fmul_rn(wgt(i), rd);
+  }
+  const typename C::T e = C::enc(val, ref);
   if (PARITY == 0)
-    pop_base(f, g, 0, 0, 0)[(s * kQ + opp(i)) * kTile] = val;
+    pop_base(f, g, 0, 0, 0)[(s * kQ + opp(i)) * kTile] = e;
   else
-    pop_base(f, g, cx(i), cy(i), cz(i))[(s * kQ + i) * kTile] = val;
+    pop_base(f, g, cx(i), cy(i), cz(i))[(s * kQ + i) * kTile] = e;
 }
 
 // Eq. 1 for one component: (1 - n_s)[f_i - (f_i - f^eq_i)/tau] + n_s f_opp(i)
@@ -230,8 +276,8 @@ __device__ __forceinline__ void put(float *f, const Geo &g, int s, int i,
 // The relaxation weight b = (1 - n_s) / tau is folded into the equilibrium:
 // B_i = b f^eq_i = (b w_i rho_s) [1 - 1.5 u.u + 4.5 (c_i.u)^2 +- 3 c_i.u],
 // so each population costs two fused multiply-adds on top of B_i.
-template <int PARITY>
-__device__ __forceinline__ void collide_put(const StepParams &p, float *f,
+template <int PARITY, int ST>
+__device__ __forceinline__ void collide_put(const StepParams &p, const Workspace &f,
                                             const Geo &g, int s,
                                             const float (&v)[kQ], float rho_s,
                                             const float (&u)[3], float nsx) {
@@ -251,20 +297,20 @@ __device__ __forceinline__ void collide_put(const StepParams &p, float *f,
     const float odd = (3.0f * bw) * cu;
     const float B_i = even + odd, B_j = even - odd;
     moving += B_i + B_j;
-    put<PARITY>(f, g, s, i, fmaf(a, v[i], fmaf(nsx, v[j], B_i)));
-    put<PARITY>(f, g, s, j, fmaf(a, v[j], fmaf(nsx, v[i], B_j)));
+    put<PARITY, ST>(p, f, g, s, i, fmaf(a, v[i], fmaf(nsx, v[j], B_i)), rho_s);
+    put<PARITY, ST>(p, f, g, s, j, fmaf(a, v[j], fmaf(nsx, v[i], B_j)), rho_s);
   }
   const float B_0 = br - moving;  // b rho_s minus the moving ones: sum_i B_i = b rho_s
-  put<PARITY>(f, g, s, 0, fmaf(a + nsx, v[0], B_0));
+  put<PARITY, ST>(p, f, g, s, 0, fmaf(a + nsx, v[0], B_0), rho_s);
 }
 
-template <int PARITY>
+template <int PARITY, int ST>
 __device__ __forceinline__ void collide_body(const StepParams &p,
                                              const Workspace &w, bool maybe_res,
                                              int x, int y, int z) {
   const Geo g = make_geo(p, x, y, z);
   float f1[kQ], f2[kQ];
-  load_pops<PARITY>(w.f, g, f1, f2);
+  load_pops<PARITY, ST>(p, w, g, f1, f2);
   reservoir_state(p, maybe_res, x, y, z, f1, f2);
   const float r1 = sum19(f1), r2 = sum19(f2);
   float j1[3], j2[3];
@@ -286,8 +332,8 @@ __device__ __forceinline__ void collide_body(const StepParams &p,
   }
 
   const float nsx = w.ns[g.node(0, 0, 0)];
-  collide_put<PARITY>(p, w.f, g, 0, f1, r1, u1, nsx);
-  collide_put<PARITY>(p, w.f, g, 1, f2, r2, u2, nsx);
+  collide_put<PARITY, ST>(p, w, g, 0, f1, r1, u1, nsx);
+  collide_put<PARITY, ST>(p, w, g, 1, f2, r2, u2, nsx);
 }
 
 template <int BZ>
@@ -303,7 +349,7 @@ __device__ __forceinline__ void block_coords(int &x, int &y, int &z) {
   z = blockIdx.z * kBZ + threadIdx.z;
 }
 
-template <int PARITY>
+template <int PARITY, int ST>
 __global__ void __launch_bounds__(kThreads) k_density(StepParams p, Workspace w) {
   int x, y, z;
   block_coords(x, y, z);
@@ -311,7 +357,7 @@ __global__ void __launch_bounds__(kThreads) k_density(StepParams p, Workspace w)
   if (x >= p.nx || y >= p.ny || z >= p.nz) return;
   const Geo g = make_geo(p, x, y, z);
   float v1[kQ], v2[kQ];
-  load_pops<PARITY>(w.f, g, v1, v2);
+  load_pops<PARITY, ST>(p, w, g, v1, v2);
   reservoir_state(p, maybe_res, x, y, z, v1, v2);
   w.rho[g.node(0, 0, 0)] = make_float2(sum19(v1), sum19(v2));
 }
@@ -328,26 +374,30 @@ __global__ void __launch_bounds__(kThreads) k_density(StepParams p, Workspace w)
 #ifndef HMCSC_MINB_ODD
 #define HMCSC_MINB_ODD 5
 #endif
-template <int PARITY>
+// The *_LOCAL storages also hold the destination densities for encoding
+// and get more registers (2 blocks of 256 / 4 blocks of 128 per SM).
+template <int PARITY, int ST = kF32>
 struct CollideShape {
   static constexpr int BZ = PARITY == 0 ? kBZ : HMCSC_ODD_BZ;
   static constexpr int threads = kTile * kBY * BZ;
-  static constexpr int minb = PARITY == 0 ? HMCSC_MINB_EVEN : HMCSC_MINB_ODD;
+  static constexpr int minb = PARITY == 0 ? (storage_local(ST) ? 2 : HMCSC_MINB_EVEN)
+                                          : (storage_local(ST) ? 4 : HMCSC_MINB_ODD);
 };
-template <int PARITY>
-__global__ void __launch_bounds__(CollideShape<PARITY>::threads, CollideShape<PARITY>::minb)
+template <int PARITY, int ST>
+__global__ void __launch_bounds__(CollideShape<PARITY, ST>::threads,
+                                  CollideShape<PARITY, ST>::minb)
     k_collide_stream(StepParams p, Workspace w) {
   const int x = blockIdx.x * kTile + threadIdx.x;
   const int y = blockIdx.y * kBY + threadIdx.y;
   const int z = blockIdx.z * CollideShape<PARITY>::BZ + threadIdx.z;
   const bool maybe_res = block_in_reservoir<CollideShape<PARITY>::BZ>(p);
   if (x >= p.nx || y >= p.ny || z >= p.nz) return;
-  collide_body<PARITY>(p, w, maybe_res, x, y, z);
+  collide_body<PARITY, ST>(p, w, maybe_res, x, y, z);
 }
 
 // Macroscopic fields of the current state into the linear staging planes:
 // rho_1, rho_2, u_macro (Eq. 7) x, y, z, p (Eq. A.6).
-template <int PARITY>
+template <int PARITY, int ST>
 __global__ void __launch_bounds__(kThreads) k_fields(StepParams p, Workspace w) {
   int x, y, z;
   block_coords(x, y, z);
@@ -355,7 +405,7 @@ __global__ void __launch_bounds__(kThreads) k_fields(StepParams p, Workspace w) 
   if (x >= p.nx || y >= p.ny || z >= p.nz) return;
   const Geo g = make_geo(p, x, y, z);
   float f1[kQ], f2[kQ];
-  load_pops<PARITY>(w.f, g, f1, f2);
+  load_pops<PARITY, ST>(p, w, g, f1, f2);
   reservoir_state(p, maybe_res, x, y, z, f1, f2);
   const float r1 = sum19(f1), r2 = sum19(f2);
   float j1[3], j2[3];
@@ -385,19 +435,29 @@ __device__ __forceinline__ long long tiled_of_linear(const StepParams &p,
   return (yz * p.ntx + x / kTile) * kTile + x % kTile;
 }
 
+// f_i = w_i rho_sigma at rest.  *_LOCAL storages take the initial
+// densities as the previous densities of time 0.
+template <int ST>
 __global__ void k_init_equilibrium(StepParams p, Workspace w,
                                    const float *__restrict__ rho1,
                                    const float *__restrict__ rho2) {
+  using C = Codec<ST>;
   const long long N = (long long)p.nx * p.ny * p.nz;
   for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
        n += (long long)gridDim.x * blockDim.x) {
     const long long tn = tiled_of_linear(p, n);
-    float *b = w.f + (tn / kTile) * kTileFloats + tn % kTile;
+    typename C::T *b = static_cast<typename C::T *>(w.f) + (tn / kTile) * kTileFloats + tn % kTile;
     const float r1 = rho1[n], r2 = rho2[n];
+    if (storage_local(ST)) w.rho_enc[tn] = make_float2(r1, r2);
 #pragma unroll
     for (int i = 0; i < kQ; ++i) {
-      b[i * kTile] = wgt(i) * r1;
-      b[(kQ + i) * kTile] = wgt(i) * r2;
+      float ref1 = p.ref[0][wclass(i)], ref2 = p.ref[1][wclass(i)];
+      if (storage_local(ST)) {
+        ref1 = __fmul_rn(wgt(i), r1);
+        ref2 = __fmul_rn(wgt(i), r2);
+      }
+      b[i * kTile] = C::enc(wgt(i) * r1, ref1);
+      b[(kQ + i) * kTile] = C::enc(wgt(i) * r2, ref2);
     }
   }
 }
@@ -495,8 +555,8 @@ int flat_blocks(const StepParams &p) {
 
 }  // namespace
 
-size_t workspace_bytes(long long nx, long long ny, long long nz, Workspace *out,
-                       char *base) {
+size_t workspace_bytes(long long nx, long long ny, long long nz, int storage,
+                       Workspace *out, char *base) {
   const Tiling t = tiling(nx, ny, nz);
   const size_t nt = (size_t)t.ntiles * kTile;
   size_t off = 0;
@@ -505,15 +565,17 @@ size_t workspace_bytes(long long nx, long long ny, long long nz, Workspace *out,
     off += (bytes + 255) / 256 * 256;
     return at;
   };
-  size_t o_f = take(sizeof(float) * (size_t)t.ntiles * kTileFloats);
+  size_t o_f = take((size_t)storage_bytes(storage) * (size_t)t.ntiles * kTileFloats);
   size_t o_rho = take(sizeof(float2) * nt);
+  size_t o_rho2 = take(storage_local(storage) ? sizeof(float2) * nt : 0);
   size_t o_ns = take(sizeof(float) * nt);
   size_t o_ads = take(sizeof(float) * nt);
   size_t o_stage = take(sizeof(float) * 6 * (size_t)t.nlin);
   size_t o_red = take(sizeof(double) * (kRedBlocks + 1) * kRedK);
   if (out) {
-    out->f = (float *)(base + o_f);
+    out->f = (void *)(base + o_f);
     out->rho = (float2 *)(base + o_rho);
+    out->rho_enc = storage_local(storage) ? (float2 *)(base + o_rho2) : nullptr;
     out->ns = (float *)(base + o_ns);
     out->ads = (float *)(base + o_ads);
     out->stage = (float *)(base + o_stage);
@@ -525,9 +587,32 @@ size_t workspace_bytes(long long nx, long long ny, long long nz, Workspace *out,
 cudaError_t launch_init_equilibrium(const StepParams &p, const Workspace &w,
                                     const float *rho_a, const float *rho_b,
                                     cudaStream_t s) {
-  k_init_equilibrium<<<flat_blocks(p), 256, 0, s>>>(p, w, rho_a, rho_b);
+  switch (p.storage) {
+    case kF16: k_init_equilibrium<kF16><<<flat_blocks(p), 256, 0, s>>>(p, w, rho_a, rho_b); break;
+    case kBF16: k_init_equilibrium<kBF16><<<flat_blocks(p), 256, 0, s>>>(p, w, rho_a, rho_b); break;
+    case kF16L: k_init_equilibrium<kF16L><<<flat_blocks(p), 256, 0, s>>>(p, w, rho_a, rho_b); break;
+    case kBF16L: k_init_equilibrium<kBF16L><<<flat_blocks(p), 256, 0, s>>>(p, w, rho_a, rho_b); break;
+    default: k_init_equilibrium<kF32><<<flat_blocks(p), 256, 0, s>>>(p, w, rho_a, rho_b);
+  }
   return cudaGetLastError();
 }
+
+// Kernel K templated on <parity, storage>, launched with the given shape.
+#define HMCSC_DISPATCH_ST(K, ST, grid, block, p, w, parity, s)                \
+  do {                                                                        \
+    if (parity == 0) K<0, ST><<<grid, block, 0, s>>>(p, w);                   \
+    else K<1, ST><<<grid, block, 0, s>>>(p, w);                               \
+  } while (0)
+#define HMCSC_DISPATCH(K, grid, block, p, w, parity, s)                       \
+  do {                                                                        \
+    switch ((p).storage) {                                                    \
+      case kF16: HMCSC_DISPATCH_ST(K, kF16, grid, block, p, w, parity, s); break;   \
+      case kBF16: HMCSC_DISPATCH_ST(K, kBF16, grid, block, p, w, parity, s); break; \
+      case kF16L: HMCSC_DISPATCH_ST(K, kF16L, grid, block, p, w, parity, s); break; \
+      case kBF16L: HMCSC_DISPATCH_ST(K, kBF16L, grid, block, p, w, parity, s); break; \
+      default: HMCSC_DISPATCH_ST(K, kF32, grid, block, p, w, parity, s);      \
+    }                                                                         \
+  } while (0)
 
 cudaError_t launch_geometry(const StepParams &p, const Workspace &w,
                             const float *ns_lin, const float *gads2_lin,
@@ -539,34 +624,23 @@ cudaError_t launch_geometry(const StepParams &p, const Workspace &w,
 cudaError_t launch_density(const StepParams &p, const Workspace &w, int parity,
                            cudaStream_t s) {
   const dim3 block(kTile, kBY, kBZ);
-  if (parity == 0)
-    k_density<0><<<node_grid(p), block, 0, s>>>(p, w);
-  else
-    k_density<1><<<node_grid(p), block, 0, s>>>(p, w);
+  HMCSC_DISPATCH(k_density, node_grid(p), block, p, w, parity, s);
   return cudaGetLastError();
 }
 
 cudaError_t launch_collide_stream(const StepParams &p, const Workspace &w,
                                   int parity, cudaStream_t s) {
-  if (parity == 0) {
-    constexpr int BZ = CollideShape<0>::BZ;
-    const dim3 grid(p.ntx, (p.ny + kBY - 1) / kBY, (p.nz + BZ - 1) / BZ);
-    k_collide_stream<0><<<grid, dim3(kTile, kBY, BZ), 0, s>>>(p, w);
-  } else {
-    constexpr int BZ = CollideShape<1>::BZ;
-    const dim3 grid(p.ntx, (p.ny + kBY - 1) / kBY, (p.nz + BZ - 1) / BZ);
-    k_collide_stream<1><<<grid, dim3(kTile, kBY, BZ), 0, s>>>(p, w);
-  }
+  const int BZ = parity == 0 ? CollideShape<0>::BZ : CollideShape<1>::BZ;
+  const dim3 grid(p.ntx, (p.ny + kBY - 1) / kBY, (p.nz + BZ - 1) / BZ);
+  const dim3 block(kTile, kBY, BZ);
+  HMCSC_DISPATCH(k_collide_stream, grid, block, p, w, parity, s);
   return cudaGetLastError();
 }
 
 cudaError_t launch_fields(const StepParams &p, const Workspace &w, int parity,
                           cudaStream_t s) {
   const dim3 block(kTile, kBY, kBZ);
-  if (parity == 0)
-    k_fields<0><<<node_grid(p), block, 0, s>>>(p, w);
-  else
-    k_fields<1><<<node_grid(p), block, 0, s>>>(p, w);
+  HMCSC_DISPATCH(k_fields, node_grid(p), block, p, w, parity, s);
   return cudaGetLastError();
 }
 

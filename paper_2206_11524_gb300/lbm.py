@@ -20,7 +20,11 @@ from . import build as _build
 LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_ENAN, LBM_ETIMEOUT, \
     LBM_ESTATE, LBM_EINTERNAL, LBM_ETOOLARGE = range(9)
 LBM_NOALLOC_MAX_NODES = 16777216
-LBM_STORAGE_F32 = 0
+LBM_STORAGE_F32, LBM_STORAGE_F16_OFFSET, LBM_STORAGE_BF16_OFFSET, \
+    LBM_STORAGE_F16_LOCAL, LBM_STORAGE_BF16_LOCAL = range(5)
+STORAGES = {"f32": LBM_STORAGE_F32, "f16": LBM_STORAGE_F16_OFFSET,
+            "bf16": LBM_STORAGE_BF16_OFFSET, "f16l": LBM_STORAGE_F16_LOCAL,
+            "bf16l": LBM_STORAGE_BF16_LOCAL}
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENAN",
                 5: "ETIMEOUT", 6: "ESTATE", 7: "EINTERNAL", 8: "ETOOLARGE"}
 
@@ -38,7 +42,7 @@ class lbm_params(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
                 ("nz", ctypes.c_int32), ("storage", ctypes.c_int32),
                 ("tau", ctypes.c_double * 2), ("G", ctypes.c_double),
-                ("F_ext", ctypes.c_double * 3)]
+                ("F_ext", ctypes.c_double * 3), ("rho0", ctypes.c_double * 2)]
 
 
 class lbm_observables(ctypes.Structure):
@@ -256,12 +260,14 @@ class Lattice:
     """
 
     def __init__(self, nx, ny, nz, tau=(1.0, 1.0), G=1.75, F_ext=(0, 0, 0),
-                 stream=None, device=None):
+                 stream=None, device=None, storage="f32", rho0=(0.0, 0.0)):
         import torch
         self.shape = (nz, ny, nx)
         self.N = nx * ny * nz
         p = lbm_params()
-        p.nx, p.ny, p.nz, p.storage = nx, ny, nz, LBM_STORAGE_F32
+        p.nx, p.ny, p.nz = nx, ny, nz
+        p.storage = STORAGES[storage] if isinstance(storage, str) else int(storage)
+        p.rho0[0], p.rho0[1] = rho0
         p.tau[0], p.tau[1] = tau
         p.G = G
         for d in range(3):
