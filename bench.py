@@ -225,6 +225,40 @@ def run_reference(args, world, rank):
     return 0
 
 
+def serving_leg(args):
+    """Continuous batching (16-bit local storage, batched kernels, CUDA
+    graphs) against one-at-a-time float32 runs on the same seeded trace of
+    heterogeneous requests, offered at 0.9 of the sequential capacity."""
+    from paper_2206_11524_gb300 import serve
+    reqs = serve.make_requests(n_req=args.serve_requests, seed=2206, L_min=32,
+                               L_max=args.serve_lmax, steps_min=1000,
+                               steps_max=args.serve_steps_max, base_n=args.serve_lmax)
+    work = [r.nodes * r.steps for r in reqs]
+    # calibrate the sequential capacity on a few requests of the trace
+    probe = sorted(reqs, key=lambda r: r.nodes)[len(reqs) // 2 - 1: len(reqs) // 2 + 2]
+    for r in probe:
+        r.arrival = 0.0
+    cal = serve.summarize(serve.run_sequential(probe))
+    rate = 0.9 * cal["mlups"] * 1e6 / (sum(work) / len(work))
+    import numpy as np
+    rng = np.random.default_rng(2207)
+    t = 0.0
+    for r in reqs:
+        t += float(rng.exponential(1.0 / rate))
+        r.arrival = t
+    seq = serve.summarize(serve.run_sequential(reqs))
+    srv = serve.Server(storage=args.serve_storage, tick_steps=400)
+    bat = serve.summarize(srv.run(reqs))
+    bat.update(storage=args.serve_storage, graph_launches=srv.graph_launches,
+               captures=srv.captures, ticks=srv.ticks)
+    seq.update(storage="f32")
+    return {"trace": f"{len(reqs)} requests, cubic L in [32, {args.serve_lmax}] "
+                     f"log-uniform, steps U{{1000..{args.serve_steps_max}}}, Poisson "
+                     f"arrivals at 0.9 x sequential capacity ({rate:.2f}/s), seeded "
+                     "electrode crops with per-request G and binder wettability",
+            "batched": bat, "sequential": seq}
+
+
 def run_gpu(args, world, rank, local):
     import numpy as np
     import torch
@@ -314,6 +348,9 @@ def run_gpu(args, world, rank, local):
     traffic_bpn = _profiled_traffic("collide_stream")
     if rank != 0:
         return 0
+    serving = None
+    if world == 1 and args.serve_requests > 0:
+        serving = serving_leg(args)
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         small = synth.electrode((64, 64, 64))
@@ -347,6 +384,7 @@ def run_gpu(args, world, rank, local):
         "gpu_launches": 2 * K,   # density pass + fused pass per step
         "clocks": clk,
         "cpu_baseline": cpu,
+        "serving": serving,
     }
     print(json.dumps(line), flush=True)
     lat.close()
@@ -365,6 +403,10 @@ def main(argv=None):
     ap.add_argument("--size", type=int, default=256)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=24)
+    ap.add_argument("--serve-lmax", type=int, default=160)
+    ap.add_argument("--serve-steps-max", type=int, default=6000)
+    ap.add_argument("--serve-storage", default="f16l")
     args = ap.parse_args(argv)
     world, rank, local = _dist()
     if args.impl == "reference":

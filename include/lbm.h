@@ -183,6 +183,34 @@ LBM_API lbm_status lbm_load(lbm_ctx *ctx, const void *host_buf, size_t bytes);
 /* Message of the last error on this context ("" if none). */
 LBM_API const char *lbm_last_error(const lbm_ctx *ctx);
 
+/* ---- Batched stepping of independent lattices ---------------------------
+ * Several contexts (up to LBM_BATCH_MAX, same storage kind, geometry and
+ * state set) advance together: each step is one density launch and one
+ * fused launch covering every lattice, whatever their sizes and AA
+ * parities.  Each lattice computes exactly what lbm_step computes for it
+ * alone.  Work goes on `cuda_stream`; the contexts' own streams are not
+ * used, so the caller orders the batch after earlier work on them.
+ * EINVAL: bad count, NULL or repeated context, mixed storage; ESTATE: a
+ * context without geometry or state. */
+#define LBM_BATCH_MAX 64
+LBM_API lbm_status lbm_batch_step(lbm_ctx *const *ctxs, int n, int n_steps,
+                                  void *cuda_stream);
+
+/* A CUDA graph of n_steps (even, >= 2) batched steps of the given contexts,
+ * captured on cuda_stream (not the legacy default stream).  Launching it
+ * runs those steps and advances every context's host state; it is valid as
+ * long as each context still has the time parity, density buffers and
+ * reservoirs it had at capture (after an even number of steps they return),
+ * else the launch returns ESTATE and nothing runs.  Reservoir changes must
+ * have taken effect (one step after lbm_set_bc) before capture.  The graph
+ * refers to the contexts: destroy it before them. */
+typedef struct lbm_graph lbm_graph;
+LBM_API lbm_status lbm_batch_graph_create(lbm_ctx *const *ctxs, int n,
+                                          int n_steps, void *cuda_stream,
+                                          lbm_graph **out);
+LBM_API lbm_status lbm_batch_graph_launch(lbm_graph *graph, void *cuda_stream);
+LBM_API void lbm_batch_graph_destroy(lbm_graph *graph);
+
 /* ---- Allocation-free observables -----------------------------------------
  * The paper has no counterpart to this entry point: it exists for callers
  * that cannot call cudaMalloc where they need the observables -- a host

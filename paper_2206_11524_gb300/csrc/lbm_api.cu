@@ -20,6 +20,8 @@ using hmcsc::kQ;
 using hmcsc::kRedBlocks;
 using hmcsc::kRedK;
 
+static_assert(LBM_BATCH_MAX == hmcsc::kBatchMax, "batch limit of the ABI");
+
 struct lbm_ctx {
   lbm_params params;
   hmcsc::StepParams sp;   // sp.res: reservoirs applied at the end of the last step
@@ -33,7 +35,17 @@ struct lbm_ctx {
   int64_t rho_at;        // time step of the densities in ws.rho (-1: none)
   bool have_geometry;
   bool have_state;
+  uint64_t bc_version;    // bumped by every lbm_set_bc
   std::string err;
+};
+
+struct lbm_graph {
+  std::vector<lbm_ctx *> ctxs;
+  int steps;
+  cudaGraphExec_t exec;
+  std::vector<int> parity0;       // AA parity of each lattice at capture
+  std::vector<int> enc0;          // encoding-density buffer index at capture
+  std::vector<uint64_t> bc0;      // reservoir configuration at capture
 };
 
 namespace {
@@ -231,6 +243,7 @@ lbm_status lbm_create(const lbm_params *params, void *d_workspace,
   c->rho_at = -1;
   c->have_geometry = false;
   c->have_state = false;
+  c->bc_version = 0;
   // Zero the whole workspace once so padding lanes hold defined values.
   cudaError_t e = cudaMemsetAsync(d_workspace, 0, need, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
@@ -413,6 +426,7 @@ lbm_status lbm_set_bc(lbm_ctx *c, int face, int layers, double rho_a,
   if (layers > 0 && (!(rho_a > 0) || !(rho_b > 0) || !std::isfinite(rho_a) ||
                      !std::isfinite(rho_b)))
     return fail(c, LBM_EINVAL, "reservoir densities must be finite and > 0");
+  c->bc_version += 1;
   hmcsc::Reservoirs &r = c->res_current;
   r.layers[face] = layers;
   r.rho[face][0] = layers > 0 ? (float)rho_a : 0.0f;
@@ -630,6 +644,150 @@ lbm_status lbm_load(lbm_ctx *c, const void *host_buf, size_t bytes) {
   c->rho_at = -1;
   c->have_state = true;
   return LBM_OK;
+}
+
+// ---- batched stepping ----
+
+namespace {
+
+lbm_status batch_check(lbm_ctx *const *ctxs, int n) {
+  if (!ctxs || n < 1 || n > hmcsc::kBatchMax) return LBM_EINVAL;
+  for (int k = 0; k < n; ++k) {
+    if (!ctxs[k]) return LBM_EINVAL;
+    if (!ctxs[k]->have_geometry || !ctxs[k]->have_state) return LBM_ESTATE;
+    if (ctxs[k]->sp.storage != ctxs[0]->sp.storage) return LBM_EINVAL;
+    for (int j = 0; j < k; ++j)
+      if (ctxs[j] == ctxs[k]) return LBM_EINVAL;
+  }
+  return LBM_OK;
+}
+
+// The state a lattice has after one more step (same bookkeeping as
+// lbm_collide_stream).
+void advance_one(lbm_ctx *c) {
+  c->sp.res = c->res_current;
+  if (hmcsc::storage_local(c->sp.storage)) {
+    c->enc = 1 - c->enc;
+    set_density_views(c);
+  }
+  c->rho_at = -1;
+  c->t += 1;
+}
+
+// Enqueue n_steps steps of every lattice on stream s: per step one batched
+// density pass and one batched fused pass.
+lbm_status batch_enqueue(lbm_ctx *const *ctxs, int n, int n_steps, cudaStream_t s) {
+  static thread_local hmcsc::BatchArgs a;  // ~16 KB: kept off the stack
+  for (int step = 0; step < n_steps; ++step) {
+    a.n = n;
+    a.prefix[0] = 0;
+    for (int k = 0; k < n; ++k) {
+      lbm_ctx *c = ctxs[k];
+      hmcsc::BatchItem &it = a.item[k];
+      it.p = c->sp;
+      it.w = c->ws;
+      it.parity = (int)(c->t & 1);
+      it.gx = c->sp.ntx;
+      it.gy = (c->params.ny + hmcsc::kBatchBY - 1) / hmcsc::kBatchBY;
+      a.prefix[k + 1] = a.prefix[k] + it.gx * it.gy * c->params.nz;
+    }
+    cudaError_t e = hmcsc::launch_batch_density(a, ctxs[0]->sp.storage, s);
+    if (e == cudaSuccess) e = hmcsc::launch_batch_collide(a, ctxs[0]->sp.storage, s);
+    if (e != cudaSuccess) {
+      for (int k = 0; k < n; ++k) cuda_fail(ctxs[k], e, "batched kernel");
+      return LBM_ECUDA;
+    }
+    for (int k = 0; k < n; ++k) advance_one(ctxs[k]);
+  }
+  return LBM_OK;
+}
+
+struct SavedState {
+  int64_t t, rho_at;
+  hmcsc::StepParams sp;
+  hmcsc::Workspace ws;
+  int enc;
+};
+
+}  // namespace
+
+lbm_status lbm_batch_step(lbm_ctx *const *ctxs, int n, int n_steps,
+                          void *cuda_stream) {
+  lbm_status st = batch_check(ctxs, n);
+  if (st) return st;
+  if (n_steps < 0) return LBM_EINVAL;
+  return batch_enqueue(ctxs, n, n_steps, (cudaStream_t)cuda_stream);
+}
+
+lbm_status lbm_batch_graph_create(lbm_ctx *const *ctxs, int n, int n_steps,
+                                  void *cuda_stream, lbm_graph **out) {
+  if (!out) return LBM_EINVAL;
+  *out = nullptr;
+  lbm_status st = batch_check(ctxs, n);
+  if (st) return st;
+  if (n_steps < 2 || n_steps % 2 != 0 || !cuda_stream) return LBM_EINVAL;
+  for (int k = 0; k < n; ++k)
+    if (memcmp(&ctxs[k]->sp.res, &ctxs[k]->res_current, sizeof(hmcsc::Reservoirs)) != 0)
+      return fail(ctxs[k], LBM_ESTATE, "a reservoir change is pending: step once first");
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  std::vector<SavedState> saved(n);
+  for (int k = 0; k < n; ++k)
+    saved[k] = {ctxs[k]->t, ctxs[k]->rho_at, ctxs[k]->sp, ctxs[k]->ws, ctxs[k]->enc};
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return cuda_fail(ctxs[0], e, "begin capture");
+  st = batch_enqueue(ctxs, n, n_steps, s);
+  cudaError_t e2 = cudaStreamEndCapture(s, &graph);
+  for (int k = 0; k < n; ++k) {   // nothing ran: restore the host state
+    ctxs[k]->t = saved[k].t;
+    ctxs[k]->rho_at = saved[k].rho_at;
+    ctxs[k]->sp = saved[k].sp;
+    ctxs[k]->ws = saved[k].ws;
+    ctxs[k]->enc = saved[k].enc;
+  }
+  if (st) {
+    if (graph) cudaGraphDestroy(graph);
+    return st;
+  }
+  if (e2 != cudaSuccess) return cuda_fail(ctxs[0], e2, "end capture");
+  cudaGraphExec_t exec = nullptr;
+  e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return cuda_fail(ctxs[0], e, "graph instantiate");
+  lbm_graph *g = new lbm_graph();
+  g->ctxs.assign(ctxs, ctxs + n);
+  g->steps = n_steps;
+  g->exec = exec;
+  for (int k = 0; k < n; ++k) {
+    g->parity0.push_back((int)(ctxs[k]->t & 1));
+    g->enc0.push_back(ctxs[k]->enc);
+    g->bc0.push_back(ctxs[k]->bc_version);
+  }
+  *out = g;
+  return LBM_OK;
+}
+
+lbm_status lbm_batch_graph_launch(lbm_graph *g, void *cuda_stream) {
+  if (!g) return LBM_EINVAL;
+  const size_t n = g->ctxs.size();
+  for (size_t k = 0; k < n; ++k) {
+    lbm_ctx *c = g->ctxs[k];
+    if ((int)(c->t & 1) != g->parity0[k] || c->enc != g->enc0[k] ||
+        c->bc_version != g->bc0[k] ||
+        memcmp(&c->sp.res, &c->res_current, sizeof(hmcsc::Reservoirs)) != 0)
+      return fail(c, LBM_ESTATE, "lattice changed since the graph was captured");
+  }
+  cudaError_t e = cudaGraphLaunch(g->exec, (cudaStream_t)cuda_stream);
+  if (e != cudaSuccess) return cuda_fail(g->ctxs[0], e, "graph launch");
+  for (size_t k = 0; k < n; ++k)
+    for (int s = 0; s < g->steps; ++s) advance_one(g->ctxs[k]);
+  return LBM_OK;
+}
+
+void lbm_batch_graph_destroy(lbm_graph *g) {
+  if (!g) return;
+  cudaGraphExecDestroy(g->exec);
+  delete g;
 }
 
 const char *lbm_last_error(const lbm_ctx *c) {

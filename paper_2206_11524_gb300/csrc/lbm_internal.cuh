@@ -148,6 +148,26 @@ __host__ __device__ inline Tiling tiling(long long nx, long long ny, long long n
 size_t workspace_bytes(long long nx, long long ny, long long nz, int storage,
                        Workspace *out, char *base);
 
+// Several lattices advanced by one launch per pass: block b of the grid
+// belongs to item r with prefix[r] <= b < prefix[r + 1]; an item's blocks
+// tile its lattice as 32 x 4 x 1 nodes.  Passed by value as a kernel
+// parameter (about 16 KB for kBatchMax items).
+constexpr int kBatchMax = 64;
+constexpr int kBatchBY = 4;
+struct BatchItem {
+  StepParams p;
+  Workspace w;
+  int parity;  // AA parity of this lattice's current time step
+  int gx, gy;  // blocks along x and y
+};
+struct BatchArgs {
+  int n;
+  int prefix[kBatchMax + 1];
+  BatchItem item[kBatchMax];
+};
+cudaError_t launch_batch_density(const BatchArgs &a, int storage, cudaStream_t s);
+cudaError_t launch_batch_collide(const BatchArgs &a, int storage, cudaStream_t s);
+
 // Kernel launchers (return the launch error).
 cudaError_t launch_init_equilibrium(const StepParams &p, const Workspace &w,
                                     const float *rho_a, const float *rho_b,

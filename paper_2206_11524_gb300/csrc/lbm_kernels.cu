@@ -543,6 +543,65 @@ __global__ void k_reduce_final(Workspace w) {
   w.red[kRedBlocks * kRedK + k] = t;
 }
 
+// ---- batched kernels: several lattices per launch ----
+
+__device__ __forceinline__ int batch_item_of_block(const BatchArgs &a) {
+  int lo = 0, hi = a.n - 1;
+  const int b = blockIdx.x;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (a.prefix[mid] <= b) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Node coordinates of this thread inside its item; false for padding.
+__device__ __forceinline__ bool batch_coords(const BatchArgs &a, int &r, int &x,
+                                             int &y, int &z, bool &maybe_res) {
+  r = batch_item_of_block(a);
+  const BatchItem &it = a.item[r];
+  const int lb = blockIdx.x - a.prefix[r];
+  const int bx = lb % it.gx, rest = lb / it.gx;
+  const int by = rest % it.gy, bz = rest / it.gy;
+  x = bx * kTile + threadIdx.x;
+  y = by * kBatchBY + threadIdx.y;
+  z = bz;
+  maybe_res = box_in_reservoir(it.p, bx * kTile, min(bx * kTile + kTile, it.p.nx) - 1,
+                               by * kBatchBY, min(by * kBatchBY + kBatchBY, it.p.ny) - 1,
+                               z, z);
+  return x < it.p.nx && y < it.p.ny;
+}
+
+template <int ST>
+__global__ void __launch_bounds__(kTile * kBatchBY)
+    k_batch_density(const __grid_constant__ BatchArgs a) {
+  int r, x, y, z;
+  bool maybe_res;
+  if (!batch_coords(a, r, x, y, z, maybe_res)) return;
+  const BatchItem &it = a.item[r];
+  const Geo g = make_geo(it.p, x, y, z);
+  float v1[kQ], v2[kQ];
+  if (it.parity == 0)
+    load_pops<0, ST>(it.p, it.w, g, v1, v2);
+  else
+    load_pops<1, ST>(it.p, it.w, g, v1, v2);
+  reservoir_state(it.p, maybe_res, x, y, z, v1, v2);
+  it.w.rho[g.node(0, 0, 0)] = make_float2(sum19(v1), sum19(v2));
+}
+
+template <int ST>
+__global__ void __launch_bounds__(kTile * kBatchBY, CollideShape<1, ST>::minb)
+    k_batch_collide(const __grid_constant__ BatchArgs a) {
+  int r, x, y, z;
+  bool maybe_res;
+  if (!batch_coords(a, r, x, y, z, maybe_res)) return;
+  const BatchItem &it = a.item[r];
+  if (it.parity == 0)
+    collide_body<0, ST>(it.p, it.w, maybe_res, x, y, z);
+  else
+    collide_body<1, ST>(it.p, it.w, maybe_res, x, y, z);
+}
+
 dim3 node_grid(const StepParams &p) {
   return dim3(p.ntx, (p.ny + kBY - 1) / kBY, (p.nz + kBZ - 1) / kBZ);
 }
@@ -641,6 +700,30 @@ cudaError_t launch_fields(const StepParams &p, const Workspace &w, int parity,
                           cudaStream_t s) {
   const dim3 block(kTile, kBY, kBZ);
   HMCSC_DISPATCH(k_fields, node_grid(p), block, p, w, parity, s);
+  return cudaGetLastError();
+}
+
+#define HMCSC_BATCH_LAUNCH(K, a, storage, s)                                  \
+  do {                                                                        \
+    const dim3 grid((unsigned)(a).prefix[(a).n]), block(kTile, kBatchBY, 1);  \
+    switch (storage) {                                                        \
+      case kF16: K<kF16><<<grid, block, 0, s>>>(a); break;                    \
+      case kBF16: K<kBF16><<<grid, block, 0, s>>>(a); break;                  \
+      case kF16L: K<kF16L><<<grid, block, 0, s>>>(a); break;                  \
+      case kBF16L: K<kBF16L><<<grid, block, 0, s>>>(a); break;                \
+      default: K<kF32><<<grid, block, 0, s>>>(a);                             \
+    }                                                                         \
+  } while (0)
+
+cudaError_t launch_batch_density(const BatchArgs &a, int storage, cudaStream_t s) {
+  if (a.n <= 0 || a.prefix[a.n] <= 0) return cudaSuccess;
+  HMCSC_BATCH_LAUNCH(k_batch_density, a, storage, s);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_collide(const BatchArgs &a, int storage, cudaStream_t s) {
+  if (a.n <= 0 || a.prefix[a.n] <= 0) return cudaSuccess;
+  HMCSC_BATCH_LAUNCH(k_batch_collide, a, storage, s);
   return cudaGetLastError();
 }
 

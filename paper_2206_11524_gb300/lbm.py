@@ -35,7 +35,10 @@ ABI_SYMBOLS = (
     "lbm_set_bc", "lbm_step", "lbm_density", "lbm_collide_stream", "lbm_time",
     "lbm_read_fields", "lbm_reduce", "lbm_sync", "lbm_checkpoint_bytes",
     "lbm_save", "lbm_load", "lbm_last_error", "lbm_reduce_fields_noalloc",
+    "lbm_batch_step", "lbm_batch_graph_create", "lbm_batch_graph_launch",
+    "lbm_batch_graph_destroy",
 )
+LBM_BATCH_MAX = 64
 
 
 class lbm_params(ctypes.Structure):
@@ -97,6 +100,11 @@ def load(path: str | None = None):
         "lbm_save": (ctypes.c_int, [vp, vp, ctypes.c_size_t]),
         "lbm_load": (ctypes.c_int, [vp, vp, ctypes.c_size_t]),
         "lbm_last_error": (ctypes.c_char_p, [vp]),
+        "lbm_batch_step": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.c_int, ctypes.c_int, vp]),
+        "lbm_batch_graph_create": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.c_int, ctypes.c_int,
+                                                  vp, ctypes.POINTER(vp)]),
+        "lbm_batch_graph_launch": (ctypes.c_int, [vp, vp]),
+        "lbm_batch_graph_destroy": (None, [vp]),
         "lbm_reduce_fields_noalloc": (ctypes.c_int, [vp, vp, vp, ctypes.c_int32,
                                                      ctypes.c_int32, ctypes.c_int32,
                                                      ctypes.POINTER(ctypes.c_int32),
@@ -247,6 +255,41 @@ def lbm_reduce_fields_noalloc(d_rho_a: int, d_rho_b: int, d_ns: int, nx: int,
         nx, ny, nz, lay, float(G), ctypes.c_void_p(cuda_stream),
         ctypes.byref(out))
     return st, out
+
+
+def _ctx_array(ctxs):
+    arr = (ctypes.c_void_p * len(ctxs))(*[c.value for c in ctxs])
+    return arr
+
+
+def lbm_batch_step(ctxs, n_steps, cuda_stream):
+    """Advance the contexts together (one launch per pass for all)."""
+    arr = _ctx_array(ctxs)
+    st = load().lbm_batch_step(arr, len(ctxs), int(n_steps), ctypes.c_void_p(cuda_stream))
+    if st != LBM_OK:
+        raise LbmError(st, load().lbm_last_error(ctxs[0]).decode() if ctxs else "")
+    return st
+
+
+def lbm_batch_graph_create(ctxs, n_steps, cuda_stream):
+    arr = _ctx_array(ctxs)
+    g = ctypes.c_void_p()
+    st = load().lbm_batch_graph_create(arr, len(ctxs), int(n_steps),
+                                       ctypes.c_void_p(cuda_stream), ctypes.byref(g))
+    if st != LBM_OK:
+        raise LbmError(st, load().lbm_last_error(ctxs[0]).decode() if ctxs else "")
+    return g
+
+
+def lbm_batch_graph_launch(graph, cuda_stream):
+    st = load().lbm_batch_graph_launch(graph, ctypes.c_void_p(cuda_stream))
+    if st != LBM_OK:
+        raise LbmError(st, "graph launch refused")
+    return st
+
+
+def lbm_batch_graph_destroy(graph):
+    load().lbm_batch_graph_destroy(graph)
 
 
 # ---- convenience wrapper ------------------------------------------------

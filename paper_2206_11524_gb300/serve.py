@@ -1,0 +1,277 @@
+"""Continuous-batching server for independent HMCSC simulations on one GPU.
+
+Requests (a lattice, its geometry and wettability, G, a step budget) arrive
+over time.  The server keeps every admitted simulation resident in HBM, runs
+all of them together -- one batched density launch and one batched fused
+launch per time step, captured as CUDA graphs of an even number of steps --
+admits new requests between ticks as memory and batch slots free up, and
+returns each result (the observables of its final state) as soon as its step
+budget is spent.  Host-side uploads of newly admitted requests overlap with
+the batch running on the GPU.
+
+`run_sequential` is the one-at-a-time baseline on the same arrival trace:
+each request alone, float32 storage, first come first served.
+
+Metrics: time-to-result (arrival -> result on the host) per request, its
+p50 / p99, and aggregate MLUPS = sum(nodes x steps) / makespan.
+"""
+from __future__ import annotations
+
+import math
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import lbm, params, synth
+
+
+@dataclass
+class Request:
+    rid: int
+    arrival: float          # seconds after the start of the run
+    L: int                  # cubic lattice edge
+    steps: int
+    ns: np.ndarray          # [L, L, L] float32
+    gads2: np.ndarray
+    rho_a: np.ndarray
+    rho_b: np.ndarray
+    reservoirs: dict
+    G: float = 1.75
+    tau: tuple = (1.0, 1.0)
+
+    @property
+    def nodes(self) -> int:
+        return self.L ** 3
+
+
+@dataclass
+class Result:
+    rid: int
+    arrival: float
+    admitted: float
+    finished: float
+    nodes: int
+    steps: int
+    observables: dict = field(default_factory=dict)
+
+    @property
+    def latency(self) -> float:
+        return self.finished - self.arrival
+
+
+def _crop(vol, L, offset):
+    """Periodic L^3 crop of a cubic volume at `offset` (z, y, x)."""
+    n = vol.shape[0]
+    idx = [(np.arange(L) + o) % n for o in offset]
+    return np.ascontiguousarray(vol[np.ix_(*idx)])
+
+
+def make_requests(n_req=32, seed=2206, L_min=32, L_max=192, steps_min=1000,
+                  steps_max=8000, rate_hz=None, base_n=192, porosities=(0.3, 0.4, 0.5, 0.6)):
+    """Seeded request trace: L = 4 round(exp(U(ln L_min, ln L_max)) / 4),
+    porosity bin in `porosities`, binder contact angle U(30, 90) deg, G
+    U(1.5, 2.0), steps U{steps_min..steps_max}, Poisson arrivals at rate_hz
+    (all at t = 0 if None).  Each request's microstructure is a seeded
+    periodic crop of a base electrode generated once per porosity bin, with
+    reservoirs on its own x faces."""
+    rng = np.random.default_rng(seed)
+    bases = {}
+    for k, phi in enumerate(porosities):
+        case = synth.electrode((base_n,) * 3, seed=seed + 101 * k,
+                               solid_fraction=1.0 - phi, res_layers=0)
+        bases[phi] = case
+    reqs = []
+    t = 0.0
+    for rid in range(n_req):
+        L = int(4 * round(math.exp(rng.uniform(math.log(L_min), math.log(L_max))) / 4))
+        L = max(8, min(L, base_n))
+        phi = porosities[int(rng.integers(len(porosities)))]
+        base = bases[phi]
+        off = tuple(int(v) for v in rng.integers(0, base_n, 3))
+        ns = _crop(base.ns, L, off).astype(np.float32)
+        binder = (ns > 0) & (ns < 1)
+        G = float(rng.uniform(1.5, 2.0))
+        theta = float(rng.uniform(30.0, 90.0))
+        gads2 = np.where(binder, params.gads_from_contact_angle(theta, G), 0.0).astype(np.float32)
+        ns[..., :4] = 0.0
+        ns[..., L - 4:] = 0.0
+        gads2[..., :4] = 0.0
+        gads2[..., L - 4:] = 0.0
+        rho_a = np.full((L,) * 3, synth.RHO_DIS, dtype=np.float32)
+        rho_b = np.full((L,) * 3, synth.RHO_MAJOR, dtype=np.float32)
+        rho_a[..., :4], rho_b[..., :4] = 1.04, 0.01
+        rho_a[..., L - 4:], rho_b[..., L - 4:] = 0.01, 0.99
+        res = {0: (4, 1.04, 0.01), 1: (4, 0.01, 0.99)}
+        steps = int(rng.integers(steps_min // 2, steps_max // 2 + 1)) * 2
+        if rate_hz:
+            t += float(rng.exponential(1.0 / rate_hz))
+        reqs.append(Request(rid, t, L, steps, ns, gads2, rho_a, rho_b, res, G=G))
+    return reqs
+
+
+def _lattice_for(req: Request, storage: str, stream):
+    lat = lbm.Lattice(req.L, req.L, req.L, tau=req.tau, G=req.G, stream=stream,
+                      storage=storage, rho0=(0.5, 0.5))
+    lat.set_geometry(req.ns, req.gads2)
+    for face, (Lr, a, b) in req.reservoirs.items():
+        lat.set_bc(face, Lr, a, b)
+    lat.init_equilibrium(req.rho_a, req.rho_b)
+    return lat
+
+
+def workspace_bytes(req: Request, storage: str) -> int:
+    p = lbm.lbm_params()
+    p.nx = p.ny = p.nz = req.L
+    p.storage = lbm.STORAGES[storage]
+    p.tau[0], p.tau[1] = req.tau
+    p.G = req.G
+    return lbm.lbm_workspace_bytes(p)
+
+
+@dataclass
+class _Slot:
+    req: Request
+    lat: object
+    remaining: int
+    admitted: float
+    stepped: bool = False   # first two plain steps taken (reservoirs in force)
+
+
+class Server:
+    """Continuous batching of resident simulations on the current GPU."""
+
+    def __init__(self, storage="f16l", tick_steps=400, use_graphs=True,
+                 max_batch=lbm.LBM_BATCH_MAX, hbm_budget=None, keep_state=False):
+        import torch
+        self.torch = torch
+        self.storage = storage
+        self.tick_steps = max(2, tick_steps - tick_steps % 2)
+        self.use_graphs = use_graphs
+        self.max_batch = min(max_batch, lbm.LBM_BATCH_MAX)
+        free, total = torch.cuda.mem_get_info()
+        self.budget = int(hbm_budget if hbm_budget is not None else 0.8 * free)
+        self.stream = torch.cuda.Stream()
+        self.keep_state = keep_state
+        self._graphs = {}
+        self.ticks = 0
+        self.graph_launches = 0
+        self.captures = 0
+
+    def _admit(self, pending, active, used, now):
+        while pending and pending[0].arrival <= now and len(active) < self.max_batch:
+            req = pending[0]
+            need = workspace_bytes(req, self.storage)
+            if used + need > self.budget:
+                break
+            pending.pop(0)
+            lat = _lattice_for(req, self.storage, self.torch.cuda.Stream())
+            active.append(_Slot(req, lat, req.steps, now))
+            used += need
+        return used
+
+    def _graph(self, slots, K):
+        key = (tuple(s.req.rid for s in slots), K)
+        g = self._graphs.get(key)
+        if g is None:
+            g = lbm.lbm_batch_graph_create([s.lat.ctx for s in slots], K,
+                                           self.stream.cuda_stream)
+            self._graphs[key] = g
+            self.captures += 1
+        return g
+
+    def _drop_graphs(self, rids):
+        for key in [k for k in self._graphs if set(k[0]) & rids]:
+            lbm.lbm_batch_graph_destroy(self._graphs.pop(key))
+
+    def run(self, requests):
+        torch = self.torch
+        pending = sorted(requests, key=lambda r: r.arrival)
+        active, results = [], []
+        used = 0
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        now = lambda: time.perf_counter() - t0
+        used = self._admit(pending, active, used, now())
+        while pending or active:
+            if not active:
+                time.sleep(max(0.0, pending[0].arrival - now()))
+                used = self._admit(pending, active, used, now())
+                continue
+            # Newly admitted lattices first take two plain batched steps: a
+            # graph needs their reservoirs in force, and two steps keep the
+            # remaining budget even.
+            fresh = [s for s in active if not s.stepped]
+            if fresh:
+                n = min(2, min(s.remaining for s in fresh))
+                lbm.lbm_batch_step([s.lat.ctx for s in fresh], n, self.stream.cuda_stream)
+                for s in fresh:
+                    s.stepped = True
+                    s.remaining -= n
+            ctxs = [s for s in active if s.remaining > 0]
+            K = min([self.tick_steps] + [s.remaining for s in ctxs]) if ctxs else 0
+            if ctxs and K > 0:
+                # a graph runs an even number of steps; an odd tail is stepped plainly
+                parity_ok = K >= 2
+                if self.use_graphs and parity_ok:
+                    K -= K % 2
+                    lbm.lbm_batch_graph_launch(self._graph(ctxs, K), self.stream.cuda_stream)
+                    self.graph_launches += 1
+                else:
+                    lbm.lbm_batch_step([s.lat.ctx for s in ctxs], K, self.stream.cuda_stream)
+                for s in ctxs:
+                    s.remaining -= K
+            self.ticks += 1
+            # Host work for new arrivals overlaps with the batch on the GPU.
+            used = self._admit(pending, active, used, now())
+            self.stream.synchronize()
+            done = [s for s in active if s.remaining == 0]
+            if done:
+                self._drop_graphs({s.req.rid for s in done})
+            for s in done:
+                obs = s.lat.observables()
+                if self.keep_state:
+                    obs["populations"] = s.lat.populations()
+                results.append(Result(s.req.rid, s.req.arrival, s.admitted, now(),
+                                      s.req.nodes, s.req.steps, obs))
+                used -= workspace_bytes(s.req, self.storage)
+                s.lat.close()
+                active.remove(s)
+                s.lat = None
+        for g in self._graphs.values():
+            lbm.lbm_batch_graph_destroy(g)
+        self._graphs.clear()
+        return results
+
+
+def run_sequential(requests, storage="f32"):
+    """One request at a time, first come first served, each with lbm_step."""
+    import torch
+    stream = torch.cuda.Stream()
+    results = []
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for req in sorted(requests, key=lambda r: r.arrival):
+        wait = req.arrival - (time.perf_counter() - t0)
+        if wait > 0:
+            time.sleep(wait)
+        admitted = time.perf_counter() - t0
+        lat = _lattice_for(req, storage, stream)
+        lat.step(req.steps)
+        obs = lat.observables()
+        results.append(Result(req.rid, req.arrival, admitted, time.perf_counter() - t0,
+                              req.nodes, req.steps, obs))
+        lat.close()
+    return results
+
+
+def summarize(results):
+    lat = np.array([r.latency for r in results])
+    start = min(r.arrival for r in results)
+    end = max(r.finished for r in results)
+    work = sum(r.nodes * r.steps for r in results)
+    return {"requests": len(results),
+            "p50_s": float(np.percentile(lat, 50)),
+            "p99_s": float(np.percentile(lat, 99)),
+            "makespan_s": end - start,
+            "mlups": work / (end - start) / 1e6}
