@@ -138,11 +138,13 @@ float stored_ref(const lbm_ctx *c, const float *rho_enc_host, int s, int i,
   return c->sp.ref[s][hmcsc::wclass(i)];
 }
 
-// Offset (in floats) of slot k of node (x, y, z) in the tiled population
-// layout.
+// Index (in stored values) of population (component s, direction i) = slot
+// k = s * 19 + i of node (x, y, z): tile, direction, lane, component.
 size_t pop_offset(const lbm_ctx *c, int k, long long x, long long y, long long z) {
   const long long t = x / hmcsc::kTile + c->sp.ntx * (y + (long long)c->params.ny * z);
-  return (size_t)t * hmcsc::kTileFloats + (size_t)k * hmcsc::kTile + (size_t)(x % hmcsc::kTile);
+  const int s = k / kQ, i = k % kQ;
+  return (((size_t)t * kQ + (size_t)i) * hmcsc::kTile + (size_t)(x % hmcsc::kTile)) * 2 +
+         (size_t)s;
 }
 
 int parity(const lbm_ctx *c) { return (int)(c->t & 1); }
@@ -168,7 +170,7 @@ struct CkptHeader {
   int64_t t, ntiles;
   hmcsc::Reservoirs applied;  // reservoirs whose reset ended step t
 };
-const char kMagic[8] = {'H', 'M', 'C', 'S', 'C', 'L', 'B', '2'};
+const char kMagic[8] = {'H', 'M', 'C', 'S', 'C', 'L', 'B', '3'};
 
 lbm_status sync_stream(lbm_ctx *c, const char *what) {
   cudaError_t e = cudaStreamSynchronize(c->stream);
@@ -594,7 +596,7 @@ lbm_status lbm_save(lbm_ctx *c, void *host_buf, size_t bytes) {
   CkptHeader h;
   memset(&h, 0, sizeof h);
   memcpy(h.magic, kMagic, 8);
-  h.version = 2;
+  h.version = 3;
   h.storage = c->params.storage;
   h.nx = c->params.nx;
   h.ny = c->params.ny;
@@ -621,7 +623,7 @@ lbm_status lbm_load(lbm_ctx *c, const void *host_buf, size_t bytes) {
     return fail(c, LBM_EINVAL, "checkpoint buffer too small");
   CkptHeader h;
   memcpy(&h, host_buf, sizeof h);
-  if (memcmp(h.magic, kMagic, 8) != 0 || h.version != 2)
+  if (memcmp(h.magic, kMagic, 8) != 0 || h.version != 3)
     return fail(c, LBM_EINVAL, "not a checkpoint of this library");
   if (h.nx != c->params.nx || h.ny != c->params.ny || h.nz != c->params.nz ||
       h.storage != c->params.storage || h.ntiles != c->sp.ntiles || h.t < 0)

@@ -14,12 +14,16 @@ constexpr int kQ = 19;
 constexpr int kFaces = 6;
 
 // Populations are stored in x-tiles of 32 nodes (one warp): tile
-// t = xt + ntx * (y + ny * z), xt = x / 32, and inside a tile the 38 slots
-// (sigma, i) are consecutive runs of 32 floats: f[t][sigma * 19 + i][x % 32].
-// A warp's access to one slot of its tile is one aligned 128-byte line, and
+// t = xt + ntx * (y + ny * z), xt = x / 32.  Inside a tile, slot i holds the
+// pair (f_i,1, f_i,2) of both components for each of the 32 nodes:
+// f[t][i][x % 32][sigma].  Both components of a direction always move
+// together (same source, same destination in either AA parity), so one
+// 8-byte (float32) or 4-byte (16-bit) access carries both, a warp's access
+// to one slot of its tile is one contiguous run of 256 or 128 bytes, and
 // every slot of a tile sits at a fixed offset from the tile's base.
 constexpr int kTile = 32;
-constexpr int kTileFloats = 2 * kQ * kTile;  // populations per tile
+constexpr int kTileFloats = 2 * kQ * kTile;  // population values per tile
+constexpr int kTilePairs = kQ * kTile;       // (sigma = 1, 2) pairs per tile
 
 // Population storage.  F32 stores f_i.  The 16-bit formats store an offset
 // f_i - w_i rho_ref and decode to float32 for all arithmetic:
@@ -65,6 +69,38 @@ template <> struct Codec<kBF16> {
 };
 template <> struct Codec<kF16L> : Codec<kF16> {};
 template <> struct Codec<kBF16L> : Codec<kBF16> {};
+
+// The stored pair (sigma = 1, 2) of one direction at one node.
+template <int ST> struct Codec2;
+template <> struct Codec2<kF32> {
+  using T2 = float2;
+  static __device__ __forceinline__ float2 dec(T2 v, float2) { return v; }
+  static __device__ __forceinline__ T2 enc(float f1, float f2, float2) {
+    return make_float2(f1, f2);
+  }
+};
+template <> struct Codec2<kF16> {
+  using T2 = __half2;
+  static __device__ __forceinline__ float2 dec(T2 v, float2 r) {
+    const float2 h = __half22float2(v);
+    return make_float2(fmaf(h.x, kHalfUnscale, r.x), fmaf(h.y, kHalfUnscale, r.y));
+  }
+  static __device__ __forceinline__ T2 enc(float f1, float f2, float2 r) {
+    return __floats2half2_rn((f1 - r.x) * kHalfScale, (f2 - r.y) * kHalfScale);
+  }
+};
+template <> struct Codec2<kBF16> {
+  using T2 = __nv_bfloat162;
+  static __device__ __forceinline__ float2 dec(T2 v, float2 r) {
+    const float2 h = __bfloat1622float2(v);
+    return make_float2(r.x + h.x, r.y + h.y);
+  }
+  static __device__ __forceinline__ T2 enc(float f1, float f2, float2 r) {
+    return __floats2bfloat162_rn(f1 - r.x, f2 - r.y);
+  }
+};
+template <> struct Codec2<kF16L> : Codec2<kF16> {};
+template <> struct Codec2<kBF16L> : Codec2<kBF16> {};
 
 // D3Q19 velocity set in the order of Eq. A.8: direction i + 9 is the
 // opposite of direction i (i = 1..9).

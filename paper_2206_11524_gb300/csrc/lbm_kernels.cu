@@ -22,9 +22,10 @@
 //           its post-collision f_i to slot i at n + c_i.
 // Every (slot, node) a thread writes is one it read itself, so the update is
 // race-free in place, and after an odd step the layout is natural again.
-// One warp is one tile: on even steps all 38 accesses of a thread are one
-// pointer plus a constant; on odd steps there is one pointer per neighbour
-// offset, shared by the loads and the stores at that offset.
+// One warp is one tile, and both components of a direction travel as one
+// pair: on even steps all 19 loads and 19 stores of a thread are one pointer
+// plus a constant; on odd steps there is one pointer per neighbour offset,
+// shared by the load and the store at that offset.
 #include "lbm_internal.cuh"
 
 namespace hmcsc {
@@ -45,10 +46,10 @@ struct Geo {
   __device__ __forceinline__ int node(int dx, int dy, int dz) const {
     return tile(dx, dy, dz) * kTile + ln[dx + 1];
   }
-  // float offset of slot 0 of node x + (dx, dy, dz) in the population array
+  // pair offset of slot 0 of node x + (dx, dy, dz) in the population array
   // (fits 32 bits: the host requires ntiles * 1216 < 2^32)
   __device__ __forceinline__ unsigned pop_off(int dx, int dy, int dz) const {
-    return (unsigned)tile(dx, dy, dz) * (unsigned)kTileFloats + (unsigned)ln[dx + 1];
+    return (unsigned)tile(dx, dy, dz) * (unsigned)kTilePairs + (unsigned)ln[dx + 1];
   }
 };
 
@@ -73,8 +74,8 @@ __device__ __forceinline__ Geo make_geo(const StepParams &p, int x, int y,
   return g;
 }
 
-// Lane-adjusted base of the tile holding node x + (dx, dy, dz): slot k of
-// that node is at base[k * 32].
+// Lane-adjusted base of the tile holding node x + (dx, dy, dz): the pair of
+// slot i of that node is at base[i * 32].
 template <typename T>
 __device__ __forceinline__ T *pop_base(T *f, const Geo &g, int dx, int dy,
                                        int dz) {
@@ -99,27 +100,19 @@ template <int PARITY, int ST>
 __device__ __forceinline__ void load_pops(const StepParams &p, const Workspace &w,
                                           const Geo &g, float (&v1)[kQ],
                                           float (&v2)[kQ]) {
-  using C = Codec<ST>;
-  typename C::T *f = static_cast<typename C::T *>(w.f);
+  using C = Codec2<ST>;
+  const typename C::T2 *f = static_cast<const typename C::T2 *>(w.f);
   const float2 own_prev = storage_local(ST) ? __ldg(&w.rho_enc[g.node(0, 0, 0)])
                                             : make_float2(0.f, 0.f);
-  if (PARITY == 0) {
-    const typename C::T *b = pop_base(f, g, 0, 0, 0);
 #pragma unroll
-    for (int i = 0; i < kQ; ++i) {
-      const float2 r = dec_ref<ST>(p, own_prev, i);
-      v1[i] = C::dec(b[i * kTile], r.x);
-      v2[i] = C::dec(b[(kQ + i) * kTile], r.y);
-    }
-  } else {
-#pragma unroll
-    for (int i = 0; i < kQ; ++i) {
-      // population i of node x sits in slot opp(i) of node x - c_i
-      const typename C::T *b = pop_base(f, g, -cx(i), -cy(i), -cz(i));
-      const float2 r = dec_ref<ST>(p, own_prev, i);
-      v1[i] = C::dec(b[opp(i) * kTile], r.x);
-      v2[i] = C::dec(b[(kQ + opp(i)) * kTile], r.y);
-    }
+  for (int i = 0; i < kQ; ++i) {
+    // population i of node x: slot i at x (even), slot opp(i) at x - c_i (odd)
+    const typename C::T2 raw =
+        PARITY == 0 ? pop_base(f, g, 0, 0, 0)[i * kTile]
+                    : pop_base(f, g, -cx(i), -cy(i), -cz(i))[opp(i) * kTile];
+    const float2 v = C::dec(raw, dec_ref<ST>(p, own_prev, i));
+    v1[i] = v.x;
+    v2[i] = v.y;
   }
 }
 
@@ -242,54 +235,52 @@ __device__ __forceinline__ float2 ld_late(const float2 *ptr) {
   return v;
 }
 
-// Encoding reference: w_i times the destination x + c_i's density at this
-// step (*_LOCAL; rho_s for the rest population, the densities pass's value
-// otherwise), or the constant w_i rho0_sigma (*_OFFSET).
+// Store the post-collision pair (both components) of direction i; it
+// becomes the pair of direction i of node x + c_i at t + 1.  Encoding
+// reference: w_i times the destination's density at this step (*_LOCAL;
+// rho_s for the rest population, the density pass's value otherwise), or the
+// constants w_i rho0_sigma (*_OFFSET).
 template <int PARITY, int ST>
-__device__ __forceinline__ void put(const StepParams &p, const Workspace &w,
-                                    const Geo &g, int s, int i, float val,
-                                    float rho_s) {
-  using C = Codec<ST>;
-  typename C::T *f = static_cast<typename C::T *>(w.f);
-  float ref = p.ref[s][wclass(i)];
+__device__ __forceinline__ void put2(const StepParams &p, const Workspace &w,
+                                     const Geo &g, int i, float o1, float o2,
+                                     float r1, float r2) {
+  using C = Codec2<ST>;
+  typename C::T2 *f = static_cast<typename C::T2 *>(w.f);
+  float2 ref = make_float2(p.ref[0][wclass(i)], p.ref[1][wclass(i)]);
   if (storage_local(ST)) {
-    float rd = rho_s;
-    if (i != 0) {
-      const float2 r = ld_late(&w.rho[g.node(cx(i), cy(i), cz(i))]);
-      rd = s == 0 ? r.x : r.y;
-    }
-    ref = __fmul_rn(wgt(i), rd);
+    const float2 rd = i == 0 ? make_float2(r1, r2)
+                             : ld_late(&w.rho[g.node(cx(i), cy(i), cz(i))]);
+    ref = make_float2(__fmul_rn(wgt(i), rd.x), __fmul_rn(wgt(i), rd.y));
   }
-  const typename C::T e = C::enc(val, ref);
+  const typename C::T2 e = C::enc(o1, o2, ref);
   if (PARITY == 0)
-    pop_base(f, g, 0, 0, 0)[(s * kQ + opp(i)) * kTile] = e;
+    pop_base(f, g, 0, 0, 0)[opp(i) * kTile] = e;
   else
-    pop_base(f, g, cx(i), cy(i), cz(i))[(s * kQ + i) * kTile] = e;
+    pop_base(f, g, cx(i), cy(i), cz(i))[i * kTile] = e;
 }
 
-// Eq. 1 for one component: (1 - n_s)[f_i - (f_i - f^eq_i)/tau] + n_s f_opp(i)
-// with f^eq of Eq. A.3 at (rho_s, u), computed for opposite pairs at once.
-// The rest population's equilibrium is taken as rho_s minus the other 18
-// (sum_i f^eq_i = rho_s holds exactly for Eq. A.3 on D3Q19), which keeps the
-// rounding of the float weights from leaking mass step after step.
-//
-// The relaxation weight b = (1 - n_s) / tau is folded into the equilibrium:
-// B_i = b f^eq_i = (b w_i rho_s) [1 - 1.5 u.u + 4.5 (c_i.u)^2 +- 3 c_i.u],
-// so each population costs two fused multiply-adds on top of B_i.
-template <int PARITY, int ST>
-__device__ __forceinline__ void collide_put(const StepParams &p, const Workspace &f,
-                                            const Geo &g, int s,
-                                            const float (&v)[kQ], float rho_s,
-                                            const float (&u)[3], float nsx) {
-  const float om = p.omega[s];
-  const float a = (1.0f - nsx) * (1.0f - om);
-  const float b = (1.0f - nsx) * om;
-  const float base = 1.0f - 1.5f * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
-  const float br = b * rho_s;
-  const float br18 = br * (1.0f / 18.0f), br36 = br * (1.0f / 36.0f);
-  float moving = 0.0f;  // sum of B_i over the 18 moving directions
-#pragma unroll
-  for (int i = 1; i <= 9; ++i) {
+// Eq. 1 for both components: (1 - n_s)[f_i - (f_i - f^eq_i)/tau] +
+// n_s f_opp(i) with f^eq of Eq. A.3 at (rho_s, u_s), computed for opposite
+// pairs at once.  The rest population's equilibrium is taken as rho_s minus
+// the other 18 (sum_i f^eq_i = rho_s holds exactly for Eq. A.3 on D3Q19),
+// which keeps the rounding of the float weights from leaking mass step after
+// step.  The relaxation weight b = (1 - n_s) / tau is folded into the
+// equilibrium: B_i = b f^eq_i = (b w_i rho_s)[1 - 1.5 u.u + 4.5 (c_i.u)^2
+// +- 3 c_i.u], so each population costs two fused multiply-adds on top of B_i.
+struct Relax {
+  float a, base, br, br18, br36, moving;
+  __device__ __forceinline__ Relax(float om, float nsx, float rho_s, const float (&u)[3]) {
+    a = (1.0f - nsx) * (1.0f - om);
+    const float b = (1.0f - nsx) * om;
+    base = 1.0f - 1.5f * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    br = b * rho_s;
+    br18 = br * (1.0f / 18.0f);
+    br36 = br * (1.0f / 36.0f);
+    moving = 0.0f;  // sum of B_i over the 18 moving directions
+  }
+  // post-collision values of the opposite pair (i, i + 9)
+  __device__ __forceinline__ void pair(int i, const float (&u)[3], const float (&v)[kQ],
+                                       float nsx, float &out_i, float &out_j) {
     const int j = i + 9;
     const float cu = cx(i) * u[0] + cy(i) * u[1] + cz(i) * u[2];
     const float bw = wgt(i) == (1.0f / 18.0f) ? br18 : br36;
@@ -297,11 +288,31 @@ __device__ __forceinline__ void collide_put(const StepParams &p, const Workspace
     const float odd = (3.0f * bw) * cu;
     const float B_i = even + odd, B_j = even - odd;
     moving += B_i + B_j;
-    put<PARITY, ST>(p, f, g, s, i, fmaf(a, v[i], fmaf(nsx, v[j], B_i)), rho_s);
-    put<PARITY, ST>(p, f, g, s, j, fmaf(a, v[j], fmaf(nsx, v[i], B_j)), rho_s);
+    out_i = fmaf(a, v[i], fmaf(nsx, v[j], B_i));
+    out_j = fmaf(a, v[j], fmaf(nsx, v[i], B_j));
   }
-  const float B_0 = br - moving;  // b rho_s minus the moving ones: sum_i B_i = b rho_s
-  put<PARITY, ST>(p, f, g, s, 0, fmaf(a + nsx, v[0], B_0), rho_s);
+  // post-collision rest population: B_0 = b rho_s - sum of the moving B_i
+  __device__ __forceinline__ float rest(const float (&v)[kQ], float nsx) const {
+    return fmaf(a + nsx, v[0], br - moving);
+  }
+};
+
+template <int PARITY, int ST>
+__device__ __forceinline__ void collide_put2(const StepParams &p, const Workspace &w,
+                                             const Geo &g, const float (&v1)[kQ],
+                                             const float (&v2)[kQ], float r1,
+                                             float r2, const float (&u1)[3],
+                                             const float (&u2)[3], float nsx) {
+  Relax c1(p.omega[0], nsx, r1, u1), c2(p.omega[1], nsx, r2, u2);
+#pragma unroll
+  for (int i = 1; i <= 9; ++i) {
+    float o1i, o1j, o2i, o2j;
+    c1.pair(i, u1, v1, nsx, o1i, o1j);
+    c2.pair(i, u2, v2, nsx, o2i, o2j);
+    put2<PARITY, ST>(p, w, g, i, o1i, o2i, r1, r2);
+    put2<PARITY, ST>(p, w, g, i + 9, o1j, o2j, r1, r2);
+  }
+  put2<PARITY, ST>(p, w, g, 0, c1.rest(v1, nsx), c2.rest(v2, nsx), r1, r2);
 }
 
 template <int PARITY, int ST>
@@ -332,8 +343,7 @@ __device__ __forceinline__ void collide_body(const StepParams &p,
   }
 
   const float nsx = w.ns[g.node(0, 0, 0)];
-  collide_put<PARITY, ST>(p, w, g, 0, f1, r1, u1, nsx);
-  collide_put<PARITY, ST>(p, w, g, 1, f2, r2, u2, nsx);
+  collide_put2<PARITY, ST>(p, w, g, f1, f2, r1, r2, u1, u2, nsx);
 }
 
 template <int BZ>
@@ -441,23 +451,19 @@ template <int ST>
 __global__ void k_init_equilibrium(StepParams p, Workspace w,
                                    const float *__restrict__ rho1,
                                    const float *__restrict__ rho2) {
-  using C = Codec<ST>;
+  using C = Codec2<ST>;
   const long long N = (long long)p.nx * p.ny * p.nz;
   for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
        n += (long long)gridDim.x * blockDim.x) {
     const long long tn = tiled_of_linear(p, n);
-    typename C::T *b = static_cast<typename C::T *>(w.f) + (tn / kTile) * kTileFloats + tn % kTile;
+    typename C::T2 *b = static_cast<typename C::T2 *>(w.f) + (tn / kTile) * kTilePairs + tn % kTile;
     const float r1 = rho1[n], r2 = rho2[n];
     if (storage_local(ST)) w.rho_enc[tn] = make_float2(r1, r2);
 #pragma unroll
     for (int i = 0; i < kQ; ++i) {
-      float ref1 = p.ref[0][wclass(i)], ref2 = p.ref[1][wclass(i)];
-      if (storage_local(ST)) {
-        ref1 = __fmul_rn(wgt(i), r1);
-        ref2 = __fmul_rn(wgt(i), r2);
-      }
-      b[i * kTile] = C::enc(wgt(i) * r1, ref1);
-      b[(kQ + i) * kTile] = C::enc(wgt(i) * r2, ref2);
+      float2 ref = make_float2(p.ref[0][wclass(i)], p.ref[1][wclass(i)]);
+      if (storage_local(ST)) ref = make_float2(__fmul_rn(wgt(i), r1), __fmul_rn(wgt(i), r2));
+      b[i * kTile] = C::enc(__fmul_rn(wgt(i), r1), __fmul_rn(wgt(i), r2), ref);
     }
   }
 }
