@@ -60,7 +60,7 @@ def _peaks():
 
 def _kernel_sha():
     h = hashlib.sha256()
-    for f in ("lbm_kernels.cu", "lbm_internal.cuh"):
+    for f in ("lbm_device.cuh", "lbm_internal.cuh", "lbm_storage_impl.cuh"):
         with open(os.path.join(ROOT, "paper_2206_11524_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -284,6 +284,12 @@ def run_gpu(args, world, rank, local):
     for face, (L, r1, r2) in case.reservoirs.items():
         lat.set_bc(face, L, r1, r2)
     lat.init_equilibrium(case.rho_a, case.rho_b)
+    launch = None
+    if not args.no_autotune:
+        import tempfile
+        from paper_2206_11524_gb300 import autotune
+        table = autotune.TuneTable(os.path.join(tempfile.mkdtemp(), "launch_table.json"))
+        launch = list(lat.autotune(table))
 
     for _ in range(args.warmup):
         lbm.lbm_density(ctx)
@@ -370,7 +376,8 @@ def run_gpu(args, world, rank, local):
                    "nodes": N, "global_nodes": N * world,
                    "l2": "inputs larger than L2 (working set "
                          f"{lat.workspace.numel() / 1e9:.2f} GB)",
-                   "parallelism": f"replicas x{world}"},
+                   "parallelism": f"replicas x{world}",
+                   "launch_config": launch},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak,
                      "peak_kind": f"{peak_kind} hbm_gbs",
@@ -403,6 +410,7 @@ def main(argv=None):
     ap.add_argument("--size", type=int, default=256)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=24)
     ap.add_argument("--serve-lmax", type=int, default=160)
     ap.add_argument("--serve-steps-max", type=int, default=6000)

@@ -183,6 +183,16 @@ LBM_API lbm_status lbm_load(lbm_ctx *ctx, const void *host_buf, size_t bytes);
 /* Message of the last error on this context ("" if none). */
 LBM_API const char *lbm_last_error(const lbm_ctx *ctx);
 
+/* Launch shapes of the density pass (0..LBM_DENSITY_CONFIGS-1) and of the
+ * fused pass on even and odd steps (0..LBM_COLLIDE_CONFIGS-1): thread-block
+ * shape and register budget, 0 = default.  Results do not depend on the
+ * choice; speed does (the autotuner measures them per lattice size and
+ * storage).  EINVAL if out of range. */
+#define LBM_DENSITY_CONFIGS 3
+#define LBM_COLLIDE_CONFIGS 4
+LBM_API lbm_status lbm_set_launch_config(lbm_ctx *ctx, int density_cfg,
+                                         int even_cfg, int odd_cfg);
+
 /* ---- Batched stepping of independent lattices ---------------------------
  * Several contexts (up to LBM_BATCH_MAX, same storage kind, geometry and
  * state set) advance together: each step is one density launch and one

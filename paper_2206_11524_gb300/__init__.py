@@ -6,5 +6,7 @@ Submodules:
   build   nvcc build of the CUDA library
   synth   seeded synthetic inputs (geometry, wettability, densities)
   params  host-side parameter conversions (contact angle, viscosity)
+  serve   continuous-batching server of independent simulations
+  autotune  launch-shape autotuner with a persisted table
 """
-__all__ = ["lbm", "build", "synth", "params"]
+__all__ = ["lbm", "build", "synth", "params", "serve", "autotune"]

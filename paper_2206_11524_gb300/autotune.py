@@ -1,0 +1,134 @@
+"""Autotuner of the launch shapes (thread-block shape and register budget) of
+the density pass and of the fused pass on even and odd steps.
+
+`tune(nx, ny, nz, storage)` times every shape on a scratch lattice of that
+size and storage (a synthetic gray medium with two-phase densities; the
+kernels' cost does not depend on the values) and returns the fastest.
+`TuneTable` keeps the winners in a JSON file keyed by GPU name, lattice size
+and storage, so a lattice of a known size is configured without timing
+(`apply(lattice)`).  The table lives at $HMCSC_TUNE_TABLE, else
+~/.cache/hmcsc/launch_table.json.
+"""
+from __future__ import annotations
+
+import json
+import os
+
+import numpy as np
+
+from . import lbm
+
+
+def _default_path() -> str:
+    return os.environ.get("HMCSC_TUNE_TABLE") or os.path.join(
+        os.path.expanduser("~"), ".cache", "hmcsc", "launch_table.json")
+
+
+def _key(nx, ny, nz, storage) -> str:
+    import torch
+    name = torch.cuda.get_device_name(torch.cuda.current_device())
+    return f"{name}|{nx}x{ny}x{nz}|{storage}"
+
+
+class TuneTable:
+    def __init__(self, path: str | None = None):
+        self.path = path or _default_path()
+        self.entries = {}
+        if os.path.exists(self.path):
+            try:
+                with open(self.path) as fh:
+                    self.entries = json.load(fh)
+            except (OSError, ValueError):
+                self.entries = {}
+
+    def get(self, nx, ny, nz, storage):
+        e = self.entries.get(_key(nx, ny, nz, storage))
+        return tuple(e["config"]) if e else None
+
+    def put(self, nx, ny, nz, storage, config, timings):
+        self.entries[_key(nx, ny, nz, storage)] = {"config": list(config),
+                                                   "timings_ms": timings}
+        os.makedirs(os.path.dirname(self.path) or ".", exist_ok=True)
+        tmp = self.path + f".tmp{os.getpid()}"
+        with open(tmp, "w") as fh:
+            json.dump(self.entries, fh, indent=1, sort_keys=True)
+        os.replace(tmp, self.path)
+
+
+def _scratch(nx, ny, nz, storage):
+    shape = (nz, ny, nx)
+    rng = np.random.default_rng(0)
+    lat = lbm.Lattice(nx, ny, nz, tau=(1.0, 1.0), G=1.75, storage=storage,
+                      rho0=(0.5, 0.5))
+    lat.set_geometry(np.full(shape, 0.3), np.zeros(shape))
+    ra = np.where(rng.random(shape) < 0.5, 0.99, 0.03)
+    lat.init_equilibrium(ra, 1.02 - ra)
+    return lat
+
+
+def _time(lat, fn, reps):
+    import torch
+    st = lat.stream
+    fn()  # warm-up (and the first launch of this shape)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(st)
+    for _ in range(reps):
+        fn()
+    b.record(st)
+    b.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def tune(nx, ny, nz, storage="f32", reps=10):
+    """Fastest (density, even, odd) launch shapes and all timings (ms)."""
+    lat = _scratch(nx, ny, nz, storage)
+    ctx = lat.ctx
+    timings = {"density": [], "even": [], "odd": []}
+    for d in range(lbm.LBM_DENSITY_CONFIGS):
+        lbm.lbm_set_launch_config(ctx, d, 0, 0)
+        timings["density"].append(_time(lat, lambda: lbm.lbm_density(ctx), reps))
+    best_d = int(np.argmin(timings["density"]))
+
+    def fused_only(parity):
+        # one full step to reach the wanted parity, then time the fused pass
+        # of that parity: density + fused of the other parity are untimed
+        import torch
+        ev = []
+        st = lat.stream
+        for _ in range(reps + 1):
+            if lbm.lbm_time(ctx) % 2 != parity:
+                lbm.lbm_step(ctx, 1)
+            lbm.lbm_density(ctx)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            lbm.lbm_collide_stream(ctx)
+            b.record(st)
+            ev.append((a, b))
+        torch.cuda.synchronize()
+        return float(np.mean([a.elapsed_time(b) for a, b in ev[1:]]))
+
+    for e in range(lbm.LBM_COLLIDE_CONFIGS):
+        lbm.lbm_set_launch_config(ctx, best_d, e, 0)
+        timings["even"].append(fused_only(0))
+    best_e = int(np.argmin(timings["even"]))
+    for o in range(lbm.LBM_COLLIDE_CONFIGS):
+        lbm.lbm_set_launch_config(ctx, best_d, best_e, o)
+        timings["odd"].append(fused_only(1))
+    best_o = int(np.argmin(timings["odd"]))
+    lat.close()
+    return (best_d, best_e, best_o), timings
+
+
+def apply(lattice, table: TuneTable | None = None, tune_if_missing=True):
+    """Configure `lattice` from the table, tuning (and recording) its size
+    and storage first when the table has no entry."""
+    table = table or TuneTable()
+    nz, ny, nx = lattice.shape
+    storage = lattice.storage_name
+    cfg = table.get(nx, ny, nz, storage)
+    if cfg is None and tune_if_missing:
+        cfg, timings = tune(nx, ny, nz, storage)
+        table.put(nx, ny, nz, storage, cfg, timings)
+    if cfg is not None:
+        lbm.lbm_set_launch_config(lattice.ctx, *cfg)
+    return cfg

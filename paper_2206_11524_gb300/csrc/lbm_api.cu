@@ -36,6 +36,7 @@ struct lbm_ctx {
   bool have_geometry;
   bool have_state;
   uint64_t bc_version;    // bumped by every lbm_set_bc
+  int launch_cfg[3];      // launch shapes: density, even fused, odd fused
   std::string err;
 };
 
@@ -246,6 +247,7 @@ lbm_status lbm_create(const lbm_params *params, void *d_workspace,
   c->have_geometry = false;
   c->have_state = false;
   c->bc_version = 0;
+  c->launch_cfg[0] = c->launch_cfg[1] = c->launch_cfg[2] = 0;
   // Zero the whole workspace once so padding lanes hold defined values.
   cudaError_t e = cudaMemsetAsync(d_workspace, 0, need, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
@@ -443,7 +445,7 @@ lbm_status lbm_density(lbm_ctx *c) {
   if (!c) return LBM_EINVAL;
   if (!c->have_geometry || !c->have_state)
     return fail(c, LBM_ESTATE, "set geometry and state before stepping");
-  cudaError_t e = hmcsc::launch_density(c->sp, c->ws, parity(c), c->stream);
+  cudaError_t e = hmcsc::launch_density(c->sp, c->ws, parity(c), c->launch_cfg[0], c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "density kernel");
   c->rho_at = c->t;
   return LBM_OK;
@@ -453,7 +455,8 @@ lbm_status lbm_collide_stream(lbm_ctx *c) {
   if (!c) return LBM_EINVAL;
   if (c->rho_at != c->t)
     return fail(c, LBM_ESTATE, "lbm_density must precede lbm_collide_stream");
-  cudaError_t e = hmcsc::launch_collide_stream(c->sp, c->ws, parity(c), c->stream);
+  cudaError_t e = hmcsc::launch_collide_stream(c->sp, c->ws, parity(c),
+                                                c->launch_cfg[1 + parity(c)], c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "collide/stream kernel");
   // The reservoirs in force now reset their layers at the end of this step.
   c->sp.res = c->res_current;
@@ -488,7 +491,7 @@ lbm_status lbm_read_fields(lbm_ctx *c, float *rho_a, float *rho_b, float *u,
   if (!c) return LBM_EINVAL;
   if (!c->have_geometry || !c->have_state)
     return fail(c, LBM_ESTATE, "no state set");
-  cudaError_t e = hmcsc::launch_density(c->sp, c->ws, parity(c), c->stream);
+  cudaError_t e = hmcsc::launch_density(c->sp, c->ws, parity(c), c->launch_cfg[0], c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "density kernel");
   c->rho_at = c->t;
   e = hmcsc::launch_fields(c->sp, c->ws, parity(c), c->stream);
@@ -511,7 +514,7 @@ lbm_status lbm_reduce(lbm_ctx *c, lbm_observables *out) {
   if (!out) return fail(c, LBM_EINVAL, "out is NULL");
   if (!c->have_geometry || !c->have_state)
     return fail(c, LBM_ESTATE, "no state set");
-  cudaError_t e = hmcsc::launch_density(c->sp, c->ws, parity(c), c->stream);
+  cudaError_t e = hmcsc::launch_density(c->sp, c->ws, parity(c), c->launch_cfg[0], c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "density kernel");
   c->rho_at = c->t;
   hmcsc::StepParams obs = c->sp;
@@ -790,6 +793,18 @@ void lbm_batch_graph_destroy(lbm_graph *g) {
   if (!g) return;
   cudaGraphExecDestroy(g->exec);
   delete g;
+}
+
+lbm_status lbm_set_launch_config(lbm_ctx *c, int density_cfg, int even_cfg,
+                                 int odd_cfg) {
+  if (!c) return LBM_EINVAL;
+  if (density_cfg < 0 || density_cfg >= hmcsc::kDensityConfigs || even_cfg < 0 ||
+      even_cfg >= hmcsc::kCollideConfigs || odd_cfg < 0 || odd_cfg >= hmcsc::kCollideConfigs)
+    return fail(c, LBM_EINVAL, "launch configuration out of range");
+  c->launch_cfg[0] = density_cfg;
+  c->launch_cfg[1] = even_cfg;
+  c->launch_cfg[2] = odd_cfg;
+  return LBM_OK;
 }
 
 const char *lbm_last_error(const lbm_ctx *c) {

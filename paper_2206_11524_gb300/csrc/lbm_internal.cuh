@@ -46,29 +46,8 @@ __host__ __device__ constexpr int wclass(int i) {
   return i == 0 ? 0 : ((i <= 3 || (i >= 10 && i <= 12)) ? 1 : 2);
 }
 
-template <int ST> struct Codec;
-template <> struct Codec<kF32> {
-  using T = float;
-  static __device__ __forceinline__ float dec(T v, float) { return v; }
-  static __device__ __forceinline__ T enc(float f, float) { return f; }
-};
+// Half offsets are kept scaled by 2^14 (see above).
 constexpr float kHalfScale = 16384.0f, kHalfUnscale = 1.0f / 16384.0f;
-template <> struct Codec<kF16> {
-  using T = __half;
-  static __device__ __forceinline__ float dec(T v, float ref) {
-    return ref + __half2float(v) * kHalfUnscale;
-  }
-  static __device__ __forceinline__ T enc(float f, float ref) {
-    return __float2half_rn((f - ref) * kHalfScale);
-  }
-};
-template <> struct Codec<kBF16> {
-  using T = __nv_bfloat16;
-  static __device__ __forceinline__ float dec(T v, float ref) { return ref + __bfloat162float(v); }
-  static __device__ __forceinline__ T enc(float f, float ref) { return __float2bfloat16_rn(f - ref); }
-};
-template <> struct Codec<kF16L> : Codec<kF16> {};
-template <> struct Codec<kBF16L> : Codec<kBF16> {};
 
 // The stored pair (sigma = 1, 2) of one direction at one node.
 template <int ST> struct Codec2;
@@ -204,6 +183,24 @@ struct BatchArgs {
 cudaError_t launch_batch_density(const BatchArgs &a, int storage, cudaStream_t s);
 cudaError_t launch_batch_collide(const BatchArgs &a, int storage, cudaStream_t s);
 
+// Per-storage launchers (one translation unit per storage kind).
+#define HMCSC_DECLARE_STORAGE_LAUNCHERS(SUF)                                   \
+  cudaError_t launch_density_##SUF(const StepParams &, const Workspace &, int, \
+                                   int, cudaStream_t);                         \
+  cudaError_t launch_collide_##SUF(const StepParams &, const Workspace &, int, \
+                                   int, cudaStream_t);                         \
+  cudaError_t launch_fields_##SUF(const StepParams &, const Workspace &, int,  \
+                                  cudaStream_t);                               \
+  cudaError_t launch_init_##SUF(const StepParams &, const Workspace &,         \
+                                const float *, const float *, cudaStream_t);   \
+  cudaError_t launch_batch_density_##SUF(const BatchArgs &, cudaStream_t);     \
+  cudaError_t launch_batch_collide_##SUF(const BatchArgs &, cudaStream_t);
+HMCSC_DECLARE_STORAGE_LAUNCHERS(f32)
+HMCSC_DECLARE_STORAGE_LAUNCHERS(f16)
+HMCSC_DECLARE_STORAGE_LAUNCHERS(bf16)
+HMCSC_DECLARE_STORAGE_LAUNCHERS(f16l)
+HMCSC_DECLARE_STORAGE_LAUNCHERS(bf16l)
+
 // Kernel launchers (return the launch error).
 cudaError_t launch_init_equilibrium(const StepParams &p, const Workspace &w,
                                     const float *rho_a, const float *rho_b,
@@ -211,10 +208,13 @@ cudaError_t launch_init_equilibrium(const StepParams &p, const Workspace &w,
 cudaError_t launch_geometry(const StepParams &p, const Workspace &w,
                             const float *ns_lin, const float *gads2_lin,
                             cudaStream_t s);
+// `cfg` selects the launch shape of the pass (0 = default; see
+// density_shape / collide_shape in lbm_device.cuh).
+constexpr int kDensityConfigs = 3, kCollideConfigs = 4;
 cudaError_t launch_density(const StepParams &p, const Workspace &w, int parity,
-                           cudaStream_t s);
+                           int cfg, cudaStream_t s);
 cudaError_t launch_collide_stream(const StepParams &p, const Workspace &w,
-                                  int parity, cudaStream_t s);
+                                  int parity, int cfg, cudaStream_t s);
 cudaError_t launch_fields(const StepParams &p, const Workspace &w, int parity,
                           cudaStream_t s);
 cudaError_t launch_reduce(const StepParams &p, const Workspace &w,

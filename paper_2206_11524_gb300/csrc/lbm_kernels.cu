@@ -1,441 +1,10 @@
-// lbm_kernels.cu -- sm_103a kernels of the HMCSC D3Q19 step.
-//
-// One time step is two launches:
-//   k_density        rho_sigma(x) = sum_i f_i,sigma(x)                (Eq. A.4)
-//   k_collide_stream moments, Shan-Chen forces (Eqs. 3-5), equilibrium
-//                    velocity (Eq. 6), equilibrium (Eq. A.3), gray collision
-//                    with partial bounce-back (Eq. 1) and in-place streaming
-//
-// Density reservoirs (Sec. 4) reset their layers to the equilibrium at rest
-// after every step.  No kernel writes that reset: every reader of a node's
-// populations (both passes, the fields pass, the host read-back) takes
-// f_i = w_i rho_res for a node inside a reservoir, which is the state the
-// reset defines, and what neighbours streamed into its slots is never read.
-// StepParams::res holds the reservoirs that were in effect at the end of the
-// previous step.
-//
-// Populations live in 32-node x-tiles (see lbm_internal.cuh) and stream in
-// place with the AA pattern:
-//   even t: node n reads slot i at n, writes its post-collision f_i to slot
-//           opp(i) at n (population i of node n + c_i at t + 1);
-//   odd t:  node n reads population i from slot opp(i) at n - c_i, writes
-//           its post-collision f_i to slot i at n + c_i.
-// Every (slot, node) a thread writes is one it read itself, so the update is
-// race-free in place, and after an odd step the layout is natural again.
-// One warp is one tile, and both components of a direction travel as one
-// pair: on even steps all 19 loads and 19 stores of a thread are one pointer
-// plus a constant; on odd steps there is one pointer per neighbour offset,
-// shared by the load and the store at that offset.
+// lbm_kernels.cu -- storage-independent kernels (geometry, observables)
+// and the launchers that dispatch the storage-typed passes to the
+// per-storage translation units (lbm_st_*.cu).
 #include "lbm_internal.cuh"
 
 namespace hmcsc {
 namespace {
-
-constexpr int kBY = 4, kBZ = 2;                 // block = 32 x kBY x kBZ nodes
-constexpr int kThreads = kTile * kBY * kBZ;     // 256
-
-// Periodic neighbourhood of one node in tile coordinates.
-struct Geo {
-  int tx[3], ln[3];  // tile-x index and lane of x-1, x, x+1
-  int yw[3], zw[3];  // y-1..y+1, z-1..z+1 (wrapped)
-  int tr[3][3];      // first tile of row (y', z'): ntx * (y' + ny * z')
-  __device__ __forceinline__ int tile(int dx, int dy, int dz) const {
-    return tr[dy + 1][dz + 1] + tx[dx + 1];
-  }
-  // tiled node index of x + (dx, dy, dz)
-  __device__ __forceinline__ int node(int dx, int dy, int dz) const {
-    return tile(dx, dy, dz) * kTile + ln[dx + 1];
-  }
-  // pair offset of slot 0 of node x + (dx, dy, dz) in the population array
-  // (fits 32 bits: the host requires ntiles * 1216 < 2^32)
-  __device__ __forceinline__ unsigned pop_off(int dx, int dy, int dz) const {
-    return (unsigned)tile(dx, dy, dz) * (unsigned)kTilePairs + (unsigned)ln[dx + 1];
-  }
-};
-
-__device__ __forceinline__ Geo make_geo(const StepParams &p, int x, int y,
-                                        int z) {
-  Geo g;
-  const int xm = x == 0 ? p.nx - 1 : x - 1;
-  const int xp = x == p.nx - 1 ? 0 : x + 1;
-  g.tx[0] = xm / kTile; g.ln[0] = xm % kTile;
-  g.tx[1] = x / kTile;  g.ln[1] = x % kTile;
-  g.tx[2] = xp / kTile; g.ln[2] = xp % kTile;
-  g.yw[0] = y == 0 ? p.ny - 1 : y - 1;
-  g.yw[1] = y;
-  g.yw[2] = y == p.ny - 1 ? 0 : y + 1;
-  g.zw[0] = z == 0 ? p.nz - 1 : z - 1;
-  g.zw[1] = z;
-  g.zw[2] = z == p.nz - 1 ? 0 : z + 1;
-#pragma unroll
-  for (int a = 0; a < 3; ++a)
-#pragma unroll
-    for (int b = 0; b < 3; ++b) g.tr[a][b] = p.ntx * (g.yw[a] + p.ny * g.zw[b]);
-  return g;
-}
-
-// Lane-adjusted base of the tile holding node x + (dx, dy, dz): the pair of
-// slot i of that node is at base[i * 32].
-template <typename T>
-__device__ __forceinline__ T *pop_base(T *f, const Geo &g, int dx, int dy,
-                                       int dz) {
-  return f + g.pop_off(dx, dy, dz);
-}
-
-// Decode references of population i of node x (both components): w_i times
-// the node's own previous density (*_LOCAL) or the constants (*_OFFSET).
-// The product is rounded on its own (no contraction) so that the host
-// read-back decodes identically.
-template <int ST>
-__device__ __forceinline__ float2 dec_ref(const StepParams &p, float2 own_prev,
-                                          int i) {
-  if (storage_local(ST))
-    return make_float2(__fmul_rn(wgt(i), own_prev.x), __fmul_rn(wgt(i), own_prev.y));
-  return make_float2(p.ref[0][wclass(i)], p.ref[1][wclass(i)]);
-}
-
-// The 19 populations of both components at the current time step, decoded
-// to float32.
-template <int PARITY, int ST>
-__device__ __forceinline__ void load_pops(const StepParams &p, const Workspace &w,
-                                          const Geo &g, float (&v1)[kQ],
-                                          float (&v2)[kQ]) {
-  using C = Codec2<ST>;
-  const typename C::T2 *f = static_cast<const typename C::T2 *>(w.f);
-  const float2 own_prev = storage_local(ST) ? __ldg(&w.rho_enc[g.node(0, 0, 0)])
-                                            : make_float2(0.f, 0.f);
-#pragma unroll
-  for (int i = 0; i < kQ; ++i) {
-    // population i of node x: slot i at x (even), slot opp(i) at x - c_i (odd)
-    const typename C::T2 raw =
-        PARITY == 0 ? pop_base(f, g, 0, 0, 0)[i * kTile]
-                    : pop_base(f, g, -cx(i), -cy(i), -cz(i))[opp(i) * kTile];
-    const float2 v = C::dec(raw, dec_ref<ST>(p, own_prev, i));
-    v1[i] = v.x;
-    v2[i] = v.y;
-  }
-}
-
-// Zeroth moment, summed in direction order; k_density and k_collide_stream
-// share this order so both see bit-identical densities.
-__device__ __forceinline__ float sum19(const float (&v)[kQ]) {
-  float r = v[0];
-#pragma unroll
-  for (int i = 1; i < kQ; ++i) r += v[i];
-  return r;
-}
-
-__device__ __forceinline__ void first_moment(const float (&v)[kQ],
-                                             float (&j)[3]) {
-  j[0] = j[1] = j[2] = 0.0f;
-#pragma unroll
-  for (int i = 1; i < kQ; ++i) {
-    if (cx(i)) j[0] += cx(i) > 0 ? v[i] : -v[i];
-    if (cy(i)) j[1] += cy(i) > 0 ? v[i] : -v[i];
-    if (cz(i)) j[2] += cz(i) > 0 ? v[i] : -v[i];
-  }
-}
-
-// Total force per unit mass of each component, F_tot,sigma / rho_sigma
-// (Eqs. 3-5; rho_sigma cancels against the prefactor of Eqs. 3-4 and the
-// density ratio of Eq. 5, so no division by a vanishing component density):
-//   g_1 = -G S_2 + A + F_ext / rho,   g_2 = -G S_1 - A + F_ext / rho
-// with S_sigma = sum_i w_i rho_sigma(x + c_i) c_i and A = sum_i w_i a(x + c_i)
-// c_i, a = G_ads,2 n_s (G_ads,1 = -G_ads,2, Table 1).  Opposite directions
-// are summed as pairs, so a uniform field gives exactly zero.
-__device__ __forceinline__ void force_per_mass(const StepParams &p,
-                                               const float2 *__restrict__ rho,
-                                               const float *__restrict__ ads,
-                                               const Geo &g, float rho_tot,
-                                               float (&g1)[3], float (&g2)[3]) {
-  float s1[3] = {0.f, 0.f, 0.f}, s2[3] = {0.f, 0.f, 0.f}, sa[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-  for (int i = 1; i <= 9; ++i) {
-    const int mp = g.node(cx(i), cy(i), cz(i));
-    const int mm = g.node(-cx(i), -cy(i), -cz(i));
-    const float2 rp = __ldg(&rho[mp]);
-    const float2 rm = __ldg(&rho[mm]);
-    const float ap = __ldg(&ads[mp]);
-    const float am = __ldg(&ads[mm]);
-    const float d1 = wgt(i) * (rp.x - rm.x);
-    const float d2 = wgt(i) * (rp.y - rm.y);
-    const float da = wgt(i) * (ap - am);
-    if (cx(i)) { s1[0] += cx(i) > 0 ? d1 : -d1; s2[0] += cx(i) > 0 ? d2 : -d2; sa[0] += cx(i) > 0 ? da : -da; }
-    if (cy(i)) { s1[1] += cy(i) > 0 ? d1 : -d1; s2[1] += cy(i) > 0 ? d2 : -d2; sa[1] += cy(i) > 0 ? da : -da; }
-    if (cz(i)) { s1[2] += cz(i) > 0 ? d1 : -d1; s2[2] += cz(i) > 0 ? d2 : -d2; sa[2] += cz(i) > 0 ? da : -da; }
-  }
-  const float inv_rho = 1.0f / rho_tot;
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    const float fe = p.F[d] * inv_rho;
-    g1[d] = -p.G * s2[d] + sa[d] + fe;
-    g2[d] = -p.G * s1[d] - sa[d] + fe;
-  }
-}
-
-// Reservoir face holding node (x, y, z), -1 if none; the higher face wins.
-__device__ __forceinline__ int res_face(const StepParams &p, int x, int y,
-                                        int z) {
-  const int *L = p.res.layers;
-  int face = -1;
-  if (L[0] && x < L[0]) face = 0;
-  if (L[1] && x >= p.nx - L[1]) face = 1;
-  if (L[2] && y < L[2]) face = 2;
-  if (L[3] && y >= p.ny - L[3]) face = 3;
-  if (L[4] && z < L[4]) face = 4;
-  if (L[5] && z >= p.nz - L[5]) face = 5;
-  return face;
-}
-
-// rho_res of component s on face `face` (selects, no indexed parameter load).
-__device__ __forceinline__ float res_rho(const StepParams &p, int face, int s) {
-  float r = p.res.rho[0][s];
-#pragma unroll
-  for (int k = 1; k < kFaces; ++k) r = face == k ? p.res.rho[k][s] : r;
-  return r;
-}
-
-// Does the block's box [xlo,xhi] x [ylo,yhi] x [zlo,zhi] hold a node inside
-// a reservoir?  Uniform over the block, known before any load.
-__device__ __forceinline__ bool box_in_reservoir(const StepParams &p, int xlo,
-                                                 int xhi, int ylo, int yhi,
-                                                 int zlo, int zhi) {
-  if (!p.res.any) return false;
-  const int *L = p.res.layers;
-  return (L[0] && xlo < L[0]) || (L[1] && xhi >= p.nx - L[1]) ||
-         (L[2] && ylo < L[2]) || (L[3] && yhi >= p.ny - L[3]) ||
-         (L[4] && zlo < L[4]) || (L[5] && zhi >= p.nz - L[5]);
-}
-
-// A node inside a reservoir holds the prescribed equilibrium at rest.  Only
-// blocks whose box meets a reservoir (`maybe`, block-uniform) look.
-__device__ __forceinline__ void reservoir_state(const StepParams &p, bool maybe,
-                                                int x, int y, int z,
-                                                float (&v1)[kQ], float (&v2)[kQ]) {
-  if (!maybe) return;
-  const int face = res_face(p, x, y, z);
-  if (face >= 0) {
-    const float r1 = res_rho(p, face, 0), r2 = res_rho(p, face, 1);
-#pragma unroll
-    for (int i = 0; i < kQ; ++i) {
-      v1[i] = wgt(i) * r1;
-      v2[i] = wgt(i) * r2;
-    }
-  }
-}
-
-// Store the post-collision population i of component s; it becomes
-// population i of node x + c_i at t + 1.
-// A read-only load the compiler may neither merge with an earlier load of
-// the same address nor hoist: keeps a value that is needed late from
-// occupying a register from the start of the kernel.
-__device__ __forceinline__ float2 ld_late(const float2 *ptr) {
-  float2 v;
-  asm volatile("ld.global.nc.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(ptr));
-  return v;
-}
-
-// Store the post-collision pair (both components) of direction i; it
-// becomes the pair of direction i of node x + c_i at t + 1.  Encoding
-// reference: w_i times the destination's density at this step (*_LOCAL;
-// rho_s for the rest population, the density pass's value otherwise), or the
-// constants w_i rho0_sigma (*_OFFSET).
-template <int PARITY, int ST>
-__device__ __forceinline__ void put2(const StepParams &p, const Workspace &w,
-                                     const Geo &g, int i, float o1, float o2,
-                                     float r1, float r2) {
-  using C = Codec2<ST>;
-  typename C::T2 *f = static_cast<typename C::T2 *>(w.f);
-  float2 ref = make_float2(p.ref[0][wclass(i)], p.ref[1][wclass(i)]);
-  if (storage_local(ST)) {
-    const float2 rd = i == 0 ? make_float2(r1, r2)
-                             : ld_late(&w.rho[g.node(cx(i), cy(i), cz(i))]);
-    ref = make_float2(__fmul_rn(wgt(i), rd.x), __fmul_rn(wgt(i), rd.y));
-  }
-  const typename C::T2 e = C::enc(o1, o2, ref);
-  if (PARITY == 0)
-    pop_base(f, g, 0, 0, 0)[opp(i) * kTile] = e;
-  else
-    pop_base(f, g, cx(i), cy(i), cz(i))[i * kTile] = e;
-}
-
-// Eq. 1 for both components: (1 - n_s)[f_i - (f_i - f^eq_i)/tau] +
-// n_s f_opp(i) with f^eq of Eq. A.3 at (rho_s, u_s), computed for opposite
-// pairs at once.  The rest population's equilibrium is taken as rho_s minus
-// the other 18 (sum_i f^eq_i = rho_s holds exactly for Eq. A.3 on D3Q19),
-// which keeps the rounding of the float weights from leaking mass step after
-// step.  The relaxation weight b = (1 - n_s) / tau is folded into the
-// equilibrium: B_i = b f^eq_i = (b w_i rho_s)[1 - 1.5 u.u + 4.5 (c_i.u)^2
-// +- 3 c_i.u], so each population costs two fused multiply-adds on top of B_i.
-struct Relax {
-  float a, base, br, br18, br36, moving;
-  __device__ __forceinline__ Relax(float om, float nsx, float rho_s, const float (&u)[3]) {
-    a = (1.0f - nsx) * (1.0f - om);
-    const float b = (1.0f - nsx) * om;
-    base = 1.0f - 1.5f * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
-    br = b * rho_s;
-    br18 = br * (1.0f / 18.0f);
-    br36 = br * (1.0f / 36.0f);
-    moving = 0.0f;  // sum of B_i over the 18 moving directions
-  }
-  // post-collision values of the opposite pair (i, i + 9)
-  __device__ __forceinline__ void pair(int i, const float (&u)[3], const float (&v)[kQ],
-                                       float nsx, float &out_i, float &out_j) {
-    const int j = i + 9;
-    const float cu = cx(i) * u[0] + cy(i) * u[1] + cz(i) * u[2];
-    const float bw = wgt(i) == (1.0f / 18.0f) ? br18 : br36;
-    const float even = bw * fmaf(4.5f * cu, cu, base);
-    const float odd = (3.0f * bw) * cu;
-    const float B_i = even + odd, B_j = even - odd;
-    moving += B_i + B_j;
-    out_i = fmaf(a, v[i], fmaf(nsx, v[j], B_i));
-    out_j = fmaf(a, v[j], fmaf(nsx, v[i], B_j));
-  }
-  // post-collision rest population: B_0 = b rho_s - sum of the moving B_i
-  __device__ __forceinline__ float rest(const float (&v)[kQ], float nsx) const {
-    return fmaf(a + nsx, v[0], br - moving);
-  }
-};
-
-template <int PARITY, int ST>
-__device__ __forceinline__ void collide_put2(const StepParams &p, const Workspace &w,
-                                             const Geo &g, const float (&v1)[kQ],
-                                             const float (&v2)[kQ], float r1,
-                                             float r2, const float (&u1)[3],
-                                             const float (&u2)[3], float nsx) {
-  Relax c1(p.omega[0], nsx, r1, u1), c2(p.omega[1], nsx, r2, u2);
-#pragma unroll
-  for (int i = 1; i <= 9; ++i) {
-    float o1i, o1j, o2i, o2j;
-    c1.pair(i, u1, v1, nsx, o1i, o1j);
-    c2.pair(i, u2, v2, nsx, o2i, o2j);
-    put2<PARITY, ST>(p, w, g, i, o1i, o2i, r1, r2);
-    put2<PARITY, ST>(p, w, g, i + 9, o1j, o2j, r1, r2);
-  }
-  put2<PARITY, ST>(p, w, g, 0, c1.rest(v1, nsx), c2.rest(v2, nsx), r1, r2);
-}
-
-template <int PARITY, int ST>
-__device__ __forceinline__ void collide_body(const StepParams &p,
-                                             const Workspace &w, bool maybe_res,
-                                             int x, int y, int z) {
-  const Geo g = make_geo(p, x, y, z);
-  float f1[kQ], f2[kQ];
-  load_pops<PARITY, ST>(p, w, g, f1, f2);
-  reservoir_state(p, maybe_res, x, y, z, f1, f2);
-  const float r1 = sum19(f1), r2 = sum19(f2);
-  float j1[3], j2[3];
-  first_moment(f1, j1);
-  first_moment(f2, j2);
-
-  float g1[3], g2[3];
-  force_per_mass(p, w.rho, w.ads, g, r1 + r2, g1, g2);
-
-  // Eq. 6: common velocity sum_s j_s/tau_s / sum_s rho_s/tau_s, then the
-  // Shan-Chen shift tau_s F_tot,s / rho_s = tau_s g_s.
-  const float inv_den = 1.0f / (r1 * p.omega[0] + r2 * p.omega[1]);
-  float u1[3], u2[3];
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    const float uc = (j1[d] * p.omega[0] + j2[d] * p.omega[1]) * inv_den;
-    u1[d] = uc + p.tau[0] * g1[d];
-    u2[d] = uc + p.tau[1] * g2[d];
-  }
-
-  const float nsx = w.ns[g.node(0, 0, 0)];
-  collide_put2<PARITY, ST>(p, w, g, f1, f2, r1, r2, u1, u2, nsx);
-}
-
-template <int BZ>
-__device__ __forceinline__ bool block_in_reservoir(const StepParams &p) {
-  const int xlo = blockIdx.x * kTile, ylo = blockIdx.y * kBY, zlo = blockIdx.z * BZ;
-  return box_in_reservoir(p, xlo, min(xlo + kTile, p.nx) - 1, ylo,
-                          min(ylo + kBY, p.ny) - 1, zlo, min(zlo + BZ, p.nz) - 1);
-}
-
-__device__ __forceinline__ void block_coords(int &x, int &y, int &z) {
-  x = blockIdx.x * kTile + threadIdx.x;
-  y = blockIdx.y * kBY + threadIdx.y;
-  z = blockIdx.z * kBZ + threadIdx.z;
-}
-
-template <int PARITY, int ST>
-__global__ void __launch_bounds__(kThreads) k_density(StepParams p, Workspace w) {
-  int x, y, z;
-  block_coords(x, y, z);
-  const bool maybe_res = block_in_reservoir<kBZ>(p);
-  if (x >= p.nx || y >= p.ny || z >= p.nz) return;
-  const Geo g = make_geo(p, x, y, z);
-  float v1[kQ], v2[kQ];
-  load_pops<PARITY, ST>(p, w, g, v1, v2);
-  reservoir_state(p, maybe_res, x, y, z, v1, v2);
-  w.rho[g.node(0, 0, 0)] = make_float2(sum19(v1), sum19(v2));
-}
-
-// Register budget per parity: the even step keeps one tile pointer and fits
-// 80 registers (3 blocks / SM); the odd step keeps one offset per neighbour
-// and gets more so that nothing spills.
-#ifndef HMCSC_MINB_EVEN
-#define HMCSC_MINB_EVEN 3
-#endif
-#ifndef HMCSC_ODD_BZ
-#define HMCSC_ODD_BZ 1
-#endif
-#ifndef HMCSC_MINB_ODD
-#define HMCSC_MINB_ODD 5
-#endif
-// The *_LOCAL storages also hold the destination densities for encoding
-// and get more registers (2 blocks of 256 / 4 blocks of 128 per SM).
-template <int PARITY, int ST = kF32>
-struct CollideShape {
-  static constexpr int BZ = PARITY == 0 ? kBZ : HMCSC_ODD_BZ;
-  static constexpr int threads = kTile * kBY * BZ;
-  static constexpr int minb = PARITY == 0 ? (storage_local(ST) ? 2 : HMCSC_MINB_EVEN)
-                                          : (storage_local(ST) ? 4 : HMCSC_MINB_ODD);
-};
-template <int PARITY, int ST>
-__global__ void __launch_bounds__(CollideShape<PARITY, ST>::threads,
-                                  CollideShape<PARITY, ST>::minb)
-    k_collide_stream(StepParams p, Workspace w) {
-  const int x = blockIdx.x * kTile + threadIdx.x;
-  const int y = blockIdx.y * kBY + threadIdx.y;
-  const int z = blockIdx.z * CollideShape<PARITY>::BZ + threadIdx.z;
-  const bool maybe_res = block_in_reservoir<CollideShape<PARITY>::BZ>(p);
-  if (x >= p.nx || y >= p.ny || z >= p.nz) return;
-  collide_body<PARITY, ST>(p, w, maybe_res, x, y, z);
-}
-
-// Macroscopic fields of the current state into the linear staging planes:
-// rho_1, rho_2, u_macro (Eq. 7) x, y, z, p (Eq. A.6).
-template <int PARITY, int ST>
-__global__ void __launch_bounds__(kThreads) k_fields(StepParams p, Workspace w) {
-  int x, y, z;
-  block_coords(x, y, z);
-  const bool maybe_res = block_in_reservoir<kBZ>(p);
-  if (x >= p.nx || y >= p.ny || z >= p.nz) return;
-  const Geo g = make_geo(p, x, y, z);
-  float f1[kQ], f2[kQ];
-  load_pops<PARITY, ST>(p, w, g, f1, f2);
-  reservoir_state(p, maybe_res, x, y, z, f1, f2);
-  const float r1 = sum19(f1), r2 = sum19(f2);
-  float j1[3], j2[3];
-  first_moment(f1, j1);
-  first_moment(f2, j2);
-  float g1[3], g2[3];
-  const float rho = r1 + r2;
-  force_per_mass(p, w.rho, w.ads, g, rho, g1, g2);
-  const float fluid = 1.0f - w.ns[g.node(0, 0, 0)];
-  const long long L = p.nlin;
-  const long long n = x + (long long)p.nx * (y + (long long)p.ny * z);
-  w.stage[n] = r1;
-  w.stage[L + n] = r2;
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    const float m = (j1[d] + 0.5f * r1 * g1[d]) + (j2[d] + 0.5f * r2 * g2[d]);
-    w.stage[(2 + d) * L + n] = fluid * m / rho;
-  }
-  w.stage[5 * L + n] = (rho + p.G * r1 * r2) * (1.0f / 3.0f);
-}
 
 // Tiled node index of linear node n = x + nx (y + ny z).
 __device__ __forceinline__ long long tiled_of_linear(const StepParams &p,
@@ -443,29 +12,6 @@ __device__ __forceinline__ long long tiled_of_linear(const StepParams &p,
   const int x = (int)(n % p.nx);
   const long long yz = n / p.nx;
   return (yz * p.ntx + x / kTile) * kTile + x % kTile;
-}
-
-// f_i = w_i rho_sigma at rest.  *_LOCAL storages take the initial
-// densities as the previous densities of time 0.
-template <int ST>
-__global__ void k_init_equilibrium(StepParams p, Workspace w,
-                                   const float *__restrict__ rho1,
-                                   const float *__restrict__ rho2) {
-  using C = Codec2<ST>;
-  const long long N = (long long)p.nx * p.ny * p.nz;
-  for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
-       n += (long long)gridDim.x * blockDim.x) {
-    const long long tn = tiled_of_linear(p, n);
-    typename C::T2 *b = static_cast<typename C::T2 *>(w.f) + (tn / kTile) * kTilePairs + tn % kTile;
-    const float r1 = rho1[n], r2 = rho2[n];
-    if (storage_local(ST)) w.rho_enc[tn] = make_float2(r1, r2);
-#pragma unroll
-    for (int i = 0; i < kQ; ++i) {
-      float2 ref = make_float2(p.ref[0][wclass(i)], p.ref[1][wclass(i)]);
-      if (storage_local(ST)) ref = make_float2(__fmul_rn(wgt(i), r1), __fmul_rn(wgt(i), r2));
-      b[i * kTile] = C::enc(__fmul_rn(wgt(i), r1), __fmul_rn(wgt(i), r2), ref);
-    }
-  }
 }
 
 // n_s and the adhesion source a = G_ads,2 n_s in tiled order.
@@ -549,69 +95,6 @@ __global__ void k_reduce_final(Workspace w) {
   w.red[kRedBlocks * kRedK + k] = t;
 }
 
-// ---- batched kernels: several lattices per launch ----
-
-__device__ __forceinline__ int batch_item_of_block(const BatchArgs &a) {
-  int lo = 0, hi = a.n - 1;
-  const int b = blockIdx.x;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (a.prefix[mid] <= b) lo = mid; else hi = mid - 1;
-  }
-  return lo;
-}
-
-// Node coordinates of this thread inside its item; false for padding.
-__device__ __forceinline__ bool batch_coords(const BatchArgs &a, int &r, int &x,
-                                             int &y, int &z, bool &maybe_res) {
-  r = batch_item_of_block(a);
-  const BatchItem &it = a.item[r];
-  const int lb = blockIdx.x - a.prefix[r];
-  const int bx = lb % it.gx, rest = lb / it.gx;
-  const int by = rest % it.gy, bz = rest / it.gy;
-  x = bx * kTile + threadIdx.x;
-  y = by * kBatchBY + threadIdx.y;
-  z = bz;
-  maybe_res = box_in_reservoir(it.p, bx * kTile, min(bx * kTile + kTile, it.p.nx) - 1,
-                               by * kBatchBY, min(by * kBatchBY + kBatchBY, it.p.ny) - 1,
-                               z, z);
-  return x < it.p.nx && y < it.p.ny;
-}
-
-template <int ST>
-__global__ void __launch_bounds__(kTile * kBatchBY)
-    k_batch_density(const __grid_constant__ BatchArgs a) {
-  int r, x, y, z;
-  bool maybe_res;
-  if (!batch_coords(a, r, x, y, z, maybe_res)) return;
-  const BatchItem &it = a.item[r];
-  const Geo g = make_geo(it.p, x, y, z);
-  float v1[kQ], v2[kQ];
-  if (it.parity == 0)
-    load_pops<0, ST>(it.p, it.w, g, v1, v2);
-  else
-    load_pops<1, ST>(it.p, it.w, g, v1, v2);
-  reservoir_state(it.p, maybe_res, x, y, z, v1, v2);
-  it.w.rho[g.node(0, 0, 0)] = make_float2(sum19(v1), sum19(v2));
-}
-
-template <int ST>
-__global__ void __launch_bounds__(kTile * kBatchBY, CollideShape<1, ST>::minb)
-    k_batch_collide(const __grid_constant__ BatchArgs a) {
-  int r, x, y, z;
-  bool maybe_res;
-  if (!batch_coords(a, r, x, y, z, maybe_res)) return;
-  const BatchItem &it = a.item[r];
-  if (it.parity == 0)
-    collide_body<0, ST>(it.p, it.w, maybe_res, x, y, z);
-  else
-    collide_body<1, ST>(it.p, it.w, maybe_res, x, y, z);
-}
-
-dim3 node_grid(const StepParams &p) {
-  return dim3(p.ntx, (p.ny + kBY - 1) / kBY, (p.nz + kBZ - 1) / kBZ);
-}
-
 int flat_blocks(const StepParams &p) {
   long long N = (long long)p.nx * p.ny * p.nz;
   long long b = (N + 255) / 256;
@@ -649,36 +132,6 @@ size_t workspace_bytes(long long nx, long long ny, long long nz, int storage,
   return off;
 }
 
-cudaError_t launch_init_equilibrium(const StepParams &p, const Workspace &w,
-                                    const float *rho_a, const float *rho_b,
-                                    cudaStream_t s) {
-  switch (p.storage) {
-    case kF16: k_init_equilibrium<kF16><<<flat_blocks(p), 256, 0, s>>>(p, w, rho_a, rho_b); break;
-    case kBF16: k_init_equilibrium<kBF16><<<flat_blocks(p), 256, 0, s>>>(p, w, rho_a, rho_b); break;
-    case kF16L: k_init_equilibrium<kF16L><<<flat_blocks(p), 256, 0, s>>>(p, w, rho_a, rho_b); break;
-    case kBF16L: k_init_equilibrium<kBF16L><<<flat_blocks(p), 256, 0, s>>>(p, w, rho_a, rho_b); break;
-    default: k_init_equilibrium<kF32><<<flat_blocks(p), 256, 0, s>>>(p, w, rho_a, rho_b);
-  }
-  return cudaGetLastError();
-}
-
-// Kernel K templated on <parity, storage>, launched with the given shape.
-#define HMCSC_DISPATCH_ST(K, ST, grid, block, p, w, parity, s)                \
-  do {                                                                        \
-    if (parity == 0) K<0, ST><<<grid, block, 0, s>>>(p, w);                   \
-    else K<1, ST><<<grid, block, 0, s>>>(p, w);                               \
-  } while (0)
-#define HMCSC_DISPATCH(K, grid, block, p, w, parity, s)                       \
-  do {                                                                        \
-    switch ((p).storage) {                                                    \
-      case kF16: HMCSC_DISPATCH_ST(K, kF16, grid, block, p, w, parity, s); break;   \
-      case kBF16: HMCSC_DISPATCH_ST(K, kBF16, grid, block, p, w, parity, s); break; \
-      case kF16L: HMCSC_DISPATCH_ST(K, kF16L, grid, block, p, w, parity, s); break; \
-      case kBF16L: HMCSC_DISPATCH_ST(K, kBF16L, grid, block, p, w, parity, s); break; \
-      default: HMCSC_DISPATCH_ST(K, kF32, grid, block, p, w, parity, s);      \
-    }                                                                         \
-  } while (0)
-
 cudaError_t launch_geometry(const StepParams &p, const Workspace &w,
                             const float *ns_lin, const float *gads2_lin,
                             cudaStream_t s) {
@@ -686,51 +139,71 @@ cudaError_t launch_geometry(const StepParams &p, const Workspace &w,
   return cudaGetLastError();
 }
 
+cudaError_t launch_init_equilibrium(const StepParams &p, const Workspace &w,
+                                    const float *rho_a, const float *rho_b,
+                                    cudaStream_t s) {
+  switch (p.storage) {
+    case kF16: return launch_init_f16(p, w, rho_a, rho_b, s);
+    case kBF16: return launch_init_bf16(p, w, rho_a, rho_b, s);
+    case kF16L: return launch_init_f16l(p, w, rho_a, rho_b, s);
+    case kBF16L: return launch_init_bf16l(p, w, rho_a, rho_b, s);
+    default: return launch_init_f32(p, w, rho_a, rho_b, s);
+  }
+}
+
 cudaError_t launch_density(const StepParams &p, const Workspace &w, int parity,
-                           cudaStream_t s) {
-  const dim3 block(kTile, kBY, kBZ);
-  HMCSC_DISPATCH(k_density, node_grid(p), block, p, w, parity, s);
-  return cudaGetLastError();
+                           int cfg, cudaStream_t s) {
+  switch (p.storage) {
+    case kF16: return launch_density_f16(p, w, parity, cfg, s);
+    case kBF16: return launch_density_bf16(p, w, parity, cfg, s);
+    case kF16L: return launch_density_f16l(p, w, parity, cfg, s);
+    case kBF16L: return launch_density_bf16l(p, w, parity, cfg, s);
+    default: return launch_density_f32(p, w, parity, cfg, s);
+  }
 }
 
 cudaError_t launch_collide_stream(const StepParams &p, const Workspace &w,
-                                  int parity, cudaStream_t s) {
-  const int BZ = parity == 0 ? CollideShape<0>::BZ : CollideShape<1>::BZ;
-  const dim3 grid(p.ntx, (p.ny + kBY - 1) / kBY, (p.nz + BZ - 1) / BZ);
-  const dim3 block(kTile, kBY, BZ);
-  HMCSC_DISPATCH(k_collide_stream, grid, block, p, w, parity, s);
-  return cudaGetLastError();
+                                  int parity, int cfg, cudaStream_t s) {
+  switch (p.storage) {
+    case kF16: return launch_collide_f16(p, w, parity, cfg, s);
+    case kBF16: return launch_collide_bf16(p, w, parity, cfg, s);
+    case kF16L: return launch_collide_f16l(p, w, parity, cfg, s);
+    case kBF16L: return launch_collide_bf16l(p, w, parity, cfg, s);
+    default: return launch_collide_f32(p, w, parity, cfg, s);
+  }
 }
 
 cudaError_t launch_fields(const StepParams &p, const Workspace &w, int parity,
                           cudaStream_t s) {
-  const dim3 block(kTile, kBY, kBZ);
-  HMCSC_DISPATCH(k_fields, node_grid(p), block, p, w, parity, s);
-  return cudaGetLastError();
+  switch (p.storage) {
+    case kF16: return launch_fields_f16(p, w, parity, s);
+    case kBF16: return launch_fields_bf16(p, w, parity, s);
+    case kF16L: return launch_fields_f16l(p, w, parity, s);
+    case kBF16L: return launch_fields_bf16l(p, w, parity, s);
+    default: return launch_fields_f32(p, w, parity, s);
+  }
 }
-
-#define HMCSC_BATCH_LAUNCH(K, a, storage, s)                                  \
-  do {                                                                        \
-    const dim3 grid((unsigned)(a).prefix[(a).n]), block(kTile, kBatchBY, 1);  \
-    switch (storage) {                                                        \
-      case kF16: K<kF16><<<grid, block, 0, s>>>(a); break;                    \
-      case kBF16: K<kBF16><<<grid, block, 0, s>>>(a); break;                  \
-      case kF16L: K<kF16L><<<grid, block, 0, s>>>(a); break;                  \
-      case kBF16L: K<kBF16L><<<grid, block, 0, s>>>(a); break;                \
-      default: K<kF32><<<grid, block, 0, s>>>(a);                             \
-    }                                                                         \
-  } while (0)
 
 cudaError_t launch_batch_density(const BatchArgs &a, int storage, cudaStream_t s) {
   if (a.n <= 0 || a.prefix[a.n] <= 0) return cudaSuccess;
-  HMCSC_BATCH_LAUNCH(k_batch_density, a, storage, s);
-  return cudaGetLastError();
+  switch (storage) {
+    case kF16: return launch_batch_density_f16(a, s);
+    case kBF16: return launch_batch_density_bf16(a, s);
+    case kF16L: return launch_batch_density_f16l(a, s);
+    case kBF16L: return launch_batch_density_bf16l(a, s);
+    default: return launch_batch_density_f32(a, s);
+  }
 }
 
 cudaError_t launch_batch_collide(const BatchArgs &a, int storage, cudaStream_t s) {
   if (a.n <= 0 || a.prefix[a.n] <= 0) return cudaSuccess;
-  HMCSC_BATCH_LAUNCH(k_batch_collide, a, storage, s);
-  return cudaGetLastError();
+  switch (storage) {
+    case kF16: return launch_batch_collide_f16(a, s);
+    case kBF16: return launch_batch_collide_bf16(a, s);
+    case kF16L: return launch_batch_collide_f16l(a, s);
+    case kBF16L: return launch_batch_collide_bf16l(a, s);
+    default: return launch_batch_collide_f32(a, s);
+  }
 }
 
 cudaError_t launch_reduce(const StepParams &p, const Workspace &w,

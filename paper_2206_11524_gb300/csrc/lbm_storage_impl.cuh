@@ -1,0 +1,87 @@
+// lbm_storage_impl.cuh -- launchers of the storage-typed kernels for one
+// storage kind.  Included once per kind by lbm_st_*.cu with HMCSC_ST (a
+// StorageKind) and HMCSC_SUF (the name suffix) defined.
+#include "lbm_device.cuh"
+
+#define HMCSC_CAT2(a, b) a##_##b
+#define HMCSC_CAT(a, b) HMCSC_CAT2(a, b)
+#define HMCSC_NAME(n) HMCSC_CAT(n, HMCSC_SUF)
+
+namespace hmcsc {
+namespace {
+constexpr int kST = HMCSC_ST;
+
+template <int PARITY, int CFG>
+void density_cfg(const StepParams &p, const Workspace &w, cudaStream_t s) {
+  constexpr Shape S = DensityShape<CFG>::s;
+  const dim3 grid(p.ntx, (p.ny + S.by - 1) / S.by, (p.nz + S.bz - 1) / S.bz);
+  k_density<PARITY, kST, CFG><<<grid, dim3(kTile, S.by, S.bz), 0, s>>>(p, w);
+}
+template <int PARITY, int CFG>
+void collide_cfg(const StepParams &p, const Workspace &w, cudaStream_t s) {
+  constexpr Shape S = CollideShape<PARITY, kST, CFG>::s;
+  const dim3 grid(p.ntx, (p.ny + S.by - 1) / S.by, (p.nz + S.bz - 1) / S.bz);
+  k_collide_stream<PARITY, kST, CFG><<<grid, dim3(kTile, S.by, S.bz), 0, s>>>(p, w);
+}
+template <int PARITY>
+void density_any(const StepParams &p, const Workspace &w, int cfg, cudaStream_t s) {
+  switch (cfg) {
+    case 1: density_cfg<PARITY, 1>(p, w, s); break;
+    case 2: density_cfg<PARITY, 2>(p, w, s); break;
+    default: density_cfg<PARITY, 0>(p, w, s);
+  }
+}
+template <int PARITY>
+void collide_any(const StepParams &p, const Workspace &w, int cfg, cudaStream_t s) {
+  switch (cfg) {
+    case 1: collide_cfg<PARITY, 1>(p, w, s); break;
+    case 2: collide_cfg<PARITY, 2>(p, w, s); break;
+    case 3: collide_cfg<PARITY, 3>(p, w, s); break;
+    default: collide_cfg<PARITY, 0>(p, w, s);
+  }
+}
+}  // namespace
+
+cudaError_t HMCSC_NAME(launch_density)(const StepParams &p, const Workspace &w,
+                                       int parity, int cfg, cudaStream_t s) {
+  if (parity == 0) density_any<0>(p, w, cfg, s); else density_any<1>(p, w, cfg, s);
+  return cudaGetLastError();
+}
+
+cudaError_t HMCSC_NAME(launch_collide)(const StepParams &p, const Workspace &w,
+                                       int parity, int cfg, cudaStream_t s) {
+  if (parity == 0) collide_any<0>(p, w, cfg, s); else collide_any<1>(p, w, cfg, s);
+  return cudaGetLastError();
+}
+
+cudaError_t HMCSC_NAME(launch_fields)(const StepParams &p, const Workspace &w,
+                                      int parity, cudaStream_t s) {
+  const dim3 grid(p.ntx, (p.ny + kFieldsBY - 1) / kFieldsBY,
+                  (p.nz + kFieldsBZ - 1) / kFieldsBZ);
+  const dim3 block(kTile, kFieldsBY, kFieldsBZ);
+  if (parity == 0) k_fields<0, kST><<<grid, block, 0, s>>>(p, w);
+  else k_fields<1, kST><<<grid, block, 0, s>>>(p, w);
+  return cudaGetLastError();
+}
+
+cudaError_t HMCSC_NAME(launch_init)(const StepParams &p, const Workspace &w,
+                                    const float *rho_a, const float *rho_b,
+                                    cudaStream_t s) {
+  const long long N = (long long)p.nx * p.ny * p.nz;
+  long long b = (N + 255) / 256;
+  b = b < 1 ? 1 : (b > 4864 ? 4864 : b);
+  k_init_equilibrium<kST><<<(unsigned)b, 256, 0, s>>>(p, w, rho_a, rho_b);
+  return cudaGetLastError();
+}
+
+cudaError_t HMCSC_NAME(launch_batch_density)(const BatchArgs &a, cudaStream_t s) {
+  k_batch_density<kST><<<(unsigned)a.prefix[a.n], dim3(kTile, kBatchBY, 1), 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t HMCSC_NAME(launch_batch_collide)(const BatchArgs &a, cudaStream_t s) {
+  k_batch_collide<kST><<<(unsigned)a.prefix[a.n], dim3(kTile, kBatchBY, 1), 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace hmcsc

@@ -36,8 +36,9 @@ ABI_SYMBOLS = (
     "lbm_read_fields", "lbm_reduce", "lbm_sync", "lbm_checkpoint_bytes",
     "lbm_save", "lbm_load", "lbm_last_error", "lbm_reduce_fields_noalloc",
     "lbm_batch_step", "lbm_batch_graph_create", "lbm_batch_graph_launch",
-    "lbm_batch_graph_destroy",
+    "lbm_batch_graph_destroy", "lbm_set_launch_config",
 )
+LBM_DENSITY_CONFIGS, LBM_COLLIDE_CONFIGS = 3, 4
 LBM_BATCH_MAX = 64
 
 
@@ -105,6 +106,7 @@ def load(path: str | None = None):
                                                   vp, ctypes.POINTER(vp)]),
         "lbm_batch_graph_launch": (ctypes.c_int, [vp, vp]),
         "lbm_batch_graph_destroy": (None, [vp]),
+        "lbm_set_launch_config": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
         "lbm_reduce_fields_noalloc": (ctypes.c_int, [vp, vp, vp, ctypes.c_int32,
                                                      ctypes.c_int32, ctypes.c_int32,
                                                      ctypes.POINTER(ctypes.c_int32),
@@ -237,6 +239,11 @@ def lbm_load(ctx, buf: bytes):
     return _check(ctx, load().lbm_load(ctx, ctypes.addressof(cbuf), len(buf)))
 
 
+def lbm_set_launch_config(ctx, density_cfg, even_cfg, odd_cfg):
+    return _check(ctx, load().lbm_set_launch_config(ctx, int(density_cfg), int(even_cfg),
+                                                    int(odd_cfg)))
+
+
 def lbm_last_error(ctx) -> str:
     msg = load().lbm_last_error(ctx)
     return msg.decode() if msg else ""
@@ -310,6 +317,7 @@ class Lattice:
         p = lbm_params()
         p.nx, p.ny, p.nz = nx, ny, nz
         p.storage = STORAGES[storage] if isinstance(storage, str) else int(storage)
+        self.storage_name = {v: k for k, v in STORAGES.items()}[p.storage]
         p.rho0[0], p.rho0[1] = rho0
         p.tau[0], p.tau[1] = tau
         p.G = G
@@ -355,6 +363,15 @@ class Lattice:
 
     def step(self, n=1):
         lbm_step(self.ctx, n)
+
+    def set_launch_config(self, density_cfg=0, even_cfg=0, odd_cfg=0):
+        lbm_set_launch_config(self.ctx, density_cfg, even_cfg, odd_cfg)
+
+    def autotune(self, table=None):
+        """Launch shapes for this size and storage from the tuning table
+        (timed on a scratch lattice first if the table has none)."""
+        from . import autotune
+        return autotune.apply(self, table)
 
     @property
     def t(self):

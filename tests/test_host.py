@@ -95,3 +95,12 @@ def test_binder_wettability_and_viscosity():
     assert abs(params.gads_from_contact_angle(60.0) - 0.214375) < 1e-12
     assert abs(params.viscosity(1.0) - 1 / 6) < 1e-15       # Table 1: 1.667e-1
     assert abs(params.permeability(0.5) - 1 / 12) < 1e-15   # Eq. 2
+
+
+def test_tune_table_persists(tmp_path, monkeypatch):
+    from paper_2206_11524_gb300 import autotune
+    monkeypatch.setattr(autotune, "_key", lambda nx, ny, nz, st: f"GPU|{nx}x{ny}x{nz}|{st}")
+    t = autotune.TuneTable(str(tmp_path / "tab.json"))
+    assert t.get(8, 8, 8, "f32") is None
+    t.put(8, 8, 8, "f32", (1, 2, 3), {"density": [0.1]})
+    assert autotune.TuneTable(str(tmp_path / "tab.json")).get(8, 8, 8, "f32") == (1, 2, 3)
