@@ -132,13 +132,22 @@ class Params:
 
 
 class Sim:
-    """Oracle simulation state.  Inputs are float64 arrays [nz, ny, nx]."""
+    """Oracle simulation state.  Inputs are float64 arrays [nz, ny, nx].
+
+    ``ns`` is the bounce-back fraction of Eq. 1: one field [nz, ny, nx] for
+    both components, or one per component [2, nz, ny, nx] (n_s,sigma)."""
 
     def __init__(self, params: Params, ns, gads2=None):
         self.p = params
         self._cp = params.c_struct()
         shape = (params.nz, params.ny, params.nx)
-        self.ns = np.ascontiguousarray(ns, dtype=np.float64).reshape(shape)
+        ns = np.asarray(ns, dtype=np.float64)
+        if ns.ndim == 4:
+            self.ns_c = np.ascontiguousarray(ns.reshape((2,) + shape))
+        else:
+            one = ns.reshape(shape)
+            self.ns_c = np.ascontiguousarray(np.stack([one, one]))
+        self.ns = self.ns_c[0]
         if gads2 is None:
             gads2 = np.zeros(shape)
         self.gads2 = np.ascontiguousarray(gads2, dtype=np.float64).reshape(shape)
@@ -168,7 +177,7 @@ class Sim:
 
     def step(self, n: int = 1):
         if n > 0:
-            _load().orc_run(ctypes.byref(self._cp), _ptr(self.ns),
+            _load().orc_run(ctypes.byref(self._cp), _ptr(self.ns_c),
                             _ptr(self.gads2), _ptr(self.f), _ptr(self._tmp),
                             _ptr(self._rho), _ptr(self._post), int(n))
         self.t += n
@@ -180,7 +189,7 @@ class Sim:
         out = {"rho_a": np.zeros(shape), "rho_b": np.zeros(shape),
                "u": np.zeros((3,) + shape), "p": np.zeros(shape),
                "ftot": np.zeros((2, 3) + shape)}
-        _load().orc_fields(ctypes.byref(self._cp), _ptr(self.ns),
+        _load().orc_fields(ctypes.byref(self._cp), _ptr(self.ns_c),
                            _ptr(self.gads2), _ptr(self.f), _ptr(self._rho),
                            _ptr(out["rho_a"]), _ptr(out["rho_b"]),
                            _ptr(out["u"]), _ptr(out["p"]), _ptr(out["ftot"]))
@@ -189,7 +198,7 @@ class Sim:
     def observables(self):
         """dict: mass (2,), sat1, p_face (6,) -- Sec. 4, Eqs. 18-19."""
         out = np.zeros(9)
-        _load().orc_observables(ctypes.byref(self._cp), _ptr(self.ns),
+        _load().orc_observables(ctypes.byref(self._cp), _ptr(self.ns_c),
                                 _ptr(self.f), _ptr(self._rho), _ptr(out))
         return {"mass": out[0:2].copy(), "sat1": float(out[2]),
                 "p_face": out[3:9].copy()}

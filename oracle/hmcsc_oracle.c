@@ -29,13 +29,20 @@
  * The lattice is periodic on every axis for streaming and for the force
  * stencils; walls are n_s = 1 cells and open faces are density reservoirs.
  *
+ * The bounce-back fraction is a field per component, n_s,sigma(x) (Eq. 1);
+ * it enters the collision of its own component, the adhesion indicator
+ * s = n_s,sigma of Eq. 4 and the fluid fraction of Eq. 7.  Arrays hold it as
+ * ns[sigma][n]; n_s,1 = n_s,2 is the common case (Table 1).
+ *
  * Readings of the paper taken here where it is silent:
  *   - the pseudopotential is the density itself (Eq. 3 uses rho);
  *   - G_ads is a per-node field, taken at the neighbour inside the sum of
  *     Eq. 4, with G_ads,1 = -G_ads,2 (Table 1);
  *   - every cell, n_s = 1 included, carries both components (Sec. 2);
  *   - reservoir corners: faces are applied in the order -x,+x,-y,+y,-z,+z,
- *     a later face overwriting an earlier one.
+ *     a later face overwriting an earlier one;
+ *   - the saturation S_1 (Eq. 19) weights a cell by the fluid fraction of
+ *     fluid 1, 1 - n_s,1.
  *
  * Build: gcc -O2 -ffp-contract=off -fPIC -shared [-fopenmp].
  */
@@ -186,8 +193,8 @@ static void moments(const orc_params *p, const double *f, int s, size_t n,
 
 /* Total force on component s at node (x,y,z), from the densities of the whole
  * lattice at the same time (rho[2][N]):
- *   F_inter,s = -rho_s G sum_i w_i rho_sbar(x + c_i) c_i            (Eq. 3)
- *   F_ads,s   = -rho_s sum_i w_i G_ads,s(x + c_i) n_s(x + c_i) c_i  (Eq. 4)
+ *   F_inter,s = -rho_s G sum_i w_i rho_sbar(x + c_i) c_i              (Eq. 3)
+ *   F_ads,s   = -rho_s sum_i w_i G_ads,s(x + c_i) n_s,s(x + c_i) c_i  (Eq. 4)
  *   F_ext,s   = rho_s / rho * F_ext                                 (Eq. 5)
  */
 static void total_force(const orc_params *p, const double *rho,
@@ -199,11 +206,11 @@ static void total_force(const orc_params *p, const double *rho,
   const double rho_s = rho[(size_t)s * N + n];
   const double rho_tot = rho[n] + rho[N + n];
   double S[3] = {0.0, 0.0, 0.0}; /* sum_i w_i rho_sbar(x+c_i) c_i      */
-  double A[3] = {0.0, 0.0, 0.0}; /* sum_i w_i Gads(x+c_i) ns(x+c_i) c_i */
+  double A[3] = {0.0, 0.0, 0.0}; /* sum_i w_i Gads(x+c_i) ns_s(x+c_i) c_i */
   for (int i = 0; i < Q; ++i) {
     size_t m = node(p, x + CX[i], y + CY[i], z + CZ[i]);
     double r = weight(i) * rho[(size_t)sb * N + m];
-    double a = weight(i) * gads_of(gads2, s, m) * ns[m];
+    double a = weight(i) * gads_of(gads2, s, m) * ns[(size_t)s * N + m];
     S[0] += r * CX[i];
     S[1] += r * CY[i];
     S[2] += r * CZ[i];
@@ -232,6 +239,8 @@ static void density_field(const orc_params *p, const double *f, double *rho) {
 
 /*
  * One time step t -> t+1.
+ *   ns    [2][N]      bounce-back fraction n_s,sigma per component
+ *   gads2 [N]         G_ads,2 per node
  *   f_in  [2][19][N]  state at t (read only)
  *   f_out [2][19][N]  state at t+1 (written)
  *   rho   [2][N]      scratch: densities at t
@@ -270,7 +279,7 @@ void orc_step(const orc_params *p, const double *ns, const double *gads2,
           double ueq[3];
           for (int d = 0; d < 3; ++d)
             ueq[d] = num[d] / den + p->tau[s] * F[s][d] / rho_s[s]; /* Eq. 6 */
-          const double nsx = ns[n];
+          const double nsx = ns[(size_t)s * N + n];
           for (int i = 0; i < Q; ++i) {
             const double fi = f_in[fidx(p, s, i, n)];
             const double fbar = f_in[fidx(p, s, opp[i], n)]; /* pre-collision */
@@ -322,7 +331,7 @@ void orc_run(const orc_params *p, const double *ns, const double *gads2,
 /*
  * Macroscopic fields of the state f at time t:
  *   rho_sigma                                                  (Eq. A.4)
- *   u_macro = 1/rho sum_s (1 - n_s)(j_s + F_tot,s / 2)         (Eq. 7)
+ *   u_macro = 1/rho sum_s (1 - n_s,s)(j_s + F_tot,s / 2)       (Eq. 7)
  *   p = c_s^2 [rho + G rho_1 rho_2]                            (Eq. A.6)
  *   F_tot,sigma                                                (Eqs. 3-5)
  * Any output pointer may be NULL.  rho_scratch: [2][N].
@@ -350,7 +359,7 @@ void orc_fields(const orc_params *p, const double *ns, const double *gads2,
           for (int d = 0; d < 3; ++d) {
             double m = 0.0;
             for (int s = 0; s < 2; ++s)
-              m += (1.0 - ns[n]) * (j_s[s][d] + F[s][d] / 2.0);
+              m += (1.0 - ns[(size_t)s * N + n]) * (j_s[s][d] + F[s][d] / 2.0);
             u[(size_t)d * N + n] = m / rho;
           }
         if (pres) pres[n] = CS2 * (rho + p->G * rho_s[0] * rho_s[1]);
@@ -365,7 +374,7 @@ void orc_fields(const orc_params *p, const double *ns, const double *gads2,
  * Scalar observables of the state f (Sec. 4):
  *   out[0], out[1]  mass of component 1 and 2: sum_x rho_sigma
  *   out[2]          saturation S_1 (Eq. 19): cells outside the reservoirs,
- *                   each weighted by its fluid fraction (1 - n_s), counted
+ *                   each weighted by its fluid-1 fraction (1 - n_s,1), counted
  *                   when rho_1 >= 0.5
  *   out[3 + k]      mean pressure (Eq. A.6) over the layers of reservoir
  *                   face k (k = 0..5: -x,+x,-y,+y,-z,+z), NaN if none;

@@ -461,3 +461,117 @@ def test_reservoir_layers_and_observables():
     assert abs(obs["sat1"] - wgt[filled].sum() / wgt.sum()) < 1e-14
     assert np.allclose(obs["mass"], [fl["rho_a"].sum(), fl["rho_b"].sum()],
                        rtol=1e-15)
+
+
+# --------------------------------------------------------------------------
+# Bounce-back fraction per component, n_s,sigma (Eq. 1, Eq. 4 with
+# s = n_s,sigma, Eq. 7; membranes of Sec. 4, porous obstacles of Sec. 3.5)
+# --------------------------------------------------------------------------
+
+def _per_component_sim(shape, ns_pair, tau, G, F, rho, u, gads=0.0):
+    nz, ny, nx = shape
+    p = oracle.Params(nx, ny, nz, tau=tau, G=G, Fext=F)
+    ns = np.stack([np.full(shape, ns_pair[0]), np.full(shape, ns_pair[1])])
+    s = oracle.Sim(p, ns, np.full(shape, gads))
+    f = np.zeros((2, 19) + shape)
+    for sg in range(2):
+        f[sg] = oracle.feq(rho[sg], np.array(u[sg], float))[:, None, None, None]
+    s.set_populations(f)
+    return s
+
+
+def _component_momentum(f):
+    c, _, _ = oracle.lattice()
+    return np.einsum("sizyx,id->sdzyx", f, c.astype(np.float64))
+
+
+@pytest.mark.parametrize("ns_pair,tau", [((0.2, 0.05), (1.0, 0.8)),
+                                         ((0.0, 0.6), (0.7, 1.4)),
+                                         ((0.9, 0.3), (1.3, 1.0))])
+def test_per_component_darcy_recurrence(ns_pair, tau):
+    """Uniform medium, uniform densities, n_s,1 != n_s,2.  Eq. 1 summed over
+    i with first-moment weights gives, per component (omega = 1/tau, bounce-
+    back reverses momentum, Eqs. 5-6 with F_inter = F_ads = 0):
+      j_s' = [(1 - n_s)(1 - omega_s) - n_s] j_s
+             + (1 - n_s) omega_s rho_s u' + (1 - n_s) rho_s F / rho,
+      u'   = (sum_s omega_s j_s) / (sum_s omega_s rho_s),
+    a 2 x 2 linear recurrence iterated here in plain float64; Eq. 7 then gives
+    rho u_macro = sum_s (1 - n_s)(j_s + rho_s F / (2 rho))."""
+    rho = (0.7, 0.3)
+    F = np.array([1e-5, -2e-5, 3e-6])
+    u0 = ((0.01, -0.02, 0.005), (-0.03, 0.01, 0.0))
+    s = _per_component_sim((3, 2, 4), ns_pair, tau, 0.5, tuple(F), rho, u0, gads=0.15)
+    om = [1.0 / t for t in tau]
+    rt = rho[0] + rho[1]
+    j = [rho[k] * np.array(u0[k]) for k in range(2)]
+    for n in range(1, 41):
+        up = (om[0] * j[0] + om[1] * j[1]) / (om[0] * rho[0] + om[1] * rho[1])
+        j = [((1 - ns_pair[k]) * (1 - om[k]) - ns_pair[k]) * j[k]
+             + (1 - ns_pair[k]) * om[k] * rho[k] * up
+             + (1 - ns_pair[k]) * rho[k] * F / rt for k in range(2)]
+        s.step(1)
+        if n in (1, 2, 7, 40):
+            got = _component_momentum(s.f)[:, :, 0, 0, 0]
+            for k in range(2):
+                assert np.allclose(got[k], j[k], rtol=1e-11, atol=1e-17), (n, k)
+            fl = s.fields()
+            rho_u = fl["u"][:, 0, 0, 0] * rt
+            expect = sum((1 - ns_pair[k]) * (j[k] + rho[k] * F / (2 * rt))
+                         for k in range(2))
+            assert np.allclose(rho_u, expect, rtol=1e-11, atol=1e-17)
+
+
+def test_membrane_blocks_only_its_component():
+    """Two membrane planes (x = 0 and x = 8: n_s,2 = 1, n_s,1 = 0) split a
+    periodic box into A (x = 1..7) and B (x = 9..15).  A full bounce-back
+    node returns every population of fluid 2 to the side it came from, so
+    fluid 2's content of B -- its densities in B plus the populations at the
+    membranes that arrived from B -- never changes, whatever G does; fluid 1
+    crosses freely and equalises between the sides (Sec. 4 membranes)."""
+    nx, shape = 16, (3, 4, 16)
+    c, _, _ = oracle.lattice()
+    x = np.arange(nx)
+    memb = (x == 0) | (x == 8)
+    B = (x >= 9)
+    ns = np.zeros((2,) + shape)
+    ns[1][..., memb] = 1.0
+    ra = np.where(B, 0.8, 0.5) * np.ones(shape)
+    rb = np.where(B, 0.1, 0.4) * np.ones(shape)
+    p = oracle.Params(nx, 4, 3, tau=(1.0, 0.9), G=0.4)
+    s = oracle.Sim(p, ns, np.zeros(shape))
+    s.init_equilibrium(ra, rb)
+
+    def content_B(f, sg):
+        tot = f[sg][..., B].sum()
+        into8 = [i for i in range(19) if c[i, 0] == -1]   # arrived at x=8 from x=9
+        into0 = [i for i in range(19) if c[i, 0] == 1]    # arrived at x=0 from x=15
+        return tot + f[sg][into8][..., 8].sum() + f[sg][into0][..., 0].sum()
+
+    m2 = content_B(s.f, 1)
+    m1 = content_B(s.f, 0)
+    s.step(300)
+    assert abs(content_B(s.f, 1) - m2) <= 1e-12 * m2
+    rho1 = s.f[0].sum(axis=0)
+    # fluid 1 has flowed from B (0.8) into A (0.5)
+    assert content_B(s.f, 0) < m1 - 0.05 * (m1 - 0.5 / 0.8 * m1)
+    assert rho1[..., 1:8].mean() > 0.52
+
+
+def test_adhesion_indicator_is_the_components_own_fraction():
+    """Eq. 4 with s = n_s,sigma: when n_s,2 is uniform its adhesion sum
+    vanishes, so F_tot,2 does not depend on G_ads while F_tot,1 (varying
+    n_s,1) does."""
+    shape = (4, 5, 6)
+    rng = np.random.default_rng(3)
+    ns = np.stack([rng.uniform(0, 0.8, shape), np.full(shape, 0.3)])
+    ra = rng.uniform(0.2, 0.8, shape)
+    rb = 1.0 - ra
+    out = []
+    for gads in (0.0, 0.12):
+        p = oracle.Params(6, 5, 4, tau=(1.0, 1.0), G=1.0)
+        s = oracle.Sim(p, ns, np.full(shape, gads))
+        s.init_equilibrium(ra, rb)
+        out.append(s.fields()["ftot"])
+    # the uniform sum vanishes up to FP64 rounding of the unpaired terms
+    assert np.abs(out[0][1] - out[1][1]).max() < 1e-15
+    assert np.abs(out[0][0] - out[1][0]).max() > 1e-3
