@@ -51,6 +51,7 @@ class _Params(ctypes.Structure):
         ("Fext", ctypes.c_double * 3),
         ("res_layers", ctypes.c_int * 6),
         ("res_rho", (ctypes.c_double * 2) * 6),
+        ("res_u", (ctypes.c_double * 3) * 6),
     ]
 
 
@@ -107,7 +108,9 @@ def feq(rho: float, u) -> np.ndarray:
 @dataclass
 class Params:
     """Model parameters (Table 1 names).  ``reservoirs`` maps a face index
-    (0..5 = -x,+x,-y,+y,-z,+z) to (layers, rho_1, rho_2)."""
+    (0..5 = -x,+x,-y,+y,-z,+z) to (layers, rho_1, rho_2) -- a density
+    reservoir at rest -- or (layers, rho_1, rho_2, (ux, uy, uz)) -- boundary
+    cells held at that velocity."""
     nx: int
     ny: int
     nz: int
@@ -124,10 +127,14 @@ class Params:
         for d in range(3):
             p.Fext[d] = self.Fext[d]
         for k in range(6):
-            layers, r1, r2 = self.reservoirs.get(k, (0, 0.0, 0.0))
+            entry = self.reservoirs.get(k, (0, 0.0, 0.0))
+            layers, r1, r2 = entry[:3]
+            u = entry[3] if len(entry) > 3 else (0.0, 0.0, 0.0)
             p.res_layers[k] = layers
             p.res_rho[k][0] = r1
             p.res_rho[k][1] = r2
+            for d in range(3):
+                p.res_u[k][d] = u[d]
         return p
 
 

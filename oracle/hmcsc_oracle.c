@@ -22,7 +22,8 @@
  *      populations (Eq. 1, Eq. A.2);
  *   6. streaming to x + c_i (left-hand side of Eq. 1);
  *   7. density reservoirs: the prescribed layers are reset to equilibrium at
- *      the prescribed densities and zero velocity (Sec. 4).
+ *      the prescribed densities and zero velocity (Sec. 4), or at a
+ *      prescribed velocity (velocity boundary cells, Sec. 3.1).
  *
  * Storage: two population buffers (the step writes a fresh buffer; pull and
  * push are not mixed), layout f[sigma][i][n], n = x + nx*(y + ny*z).
@@ -92,6 +93,9 @@ typedef struct {
   double Fext[3];    /* body force on the mixture                 (Eq. 5)  */
   int res_layers[6]; /* reservoir thickness per face, 0 = none (Sec. 4)    */
   double res_rho[6][2]; /* prescribed densities per face and component     */
+  double res_u[6][3];   /* prescribed velocity per face (0: density
+                           reservoir; nonzero: the velocity boundary cells of
+                           the Couette flow, Sec. 3.1)                      */
 } orc_params;
 
 /* Periodic wrap of one coordinate into [0, n). */
@@ -304,8 +308,8 @@ void orc_step(const orc_params *p, const double *ns, const double *gads2,
             f_out[fidx(p, s, i, to)] = post[fidx(p, s, i, from)];
           }
 
-  /* 7. reservoirs: prescribed densities at rest (Sec. 4). */
-  const double zero[3] = {0.0, 0.0, 0.0};
+  /* 7. reservoirs: prescribed densities at rest (Sec. 4) or at the
+   *    prescribed velocity of a velocity boundary (Sec. 3.1). */
   for (int z = 0; z < p->nz; ++z)
     for (int y = 0; y < p->ny; ++y)
       for (int x = 0; x < p->nx; ++x) {
@@ -314,7 +318,7 @@ void orc_step(const orc_params *p, const double *ns, const double *gads2,
         size_t n = node(p, x, y, z);
         for (int s = 0; s < 2; ++s)
           for (int i = 0; i < Q; ++i)
-            f_out[fidx(p, s, i, n)] = feq(i, p->res_rho[face][s], zero);
+            f_out[fidx(p, s, i, n)] = feq(i, p->res_rho[face][s], p->res_u[face]);
       }
 }
 

@@ -575,3 +575,51 @@ def test_adhesion_indicator_is_the_components_own_fraction():
     # the uniform sum vanishes up to FP64 rounding of the unpaired terms
     assert np.abs(out[0][1] - out[1][1]).max() < 1e-15
     assert np.abs(out[0][0] - out[1][0]).max() > 1e-3
+
+
+# --------------------------------------------------------------------------
+# Velocity boundary cells: Couette flow in a homogeneous gray medium
+# (Sec. 3.1, Eq. 14)
+# --------------------------------------------------------------------------
+
+def _couette_profile(ns, steps, H=50, U0=0.01):
+    """Channel of H + 1 node layers along x: boundary cells x = 0 (u = 0)
+    and x = H (u = U0 along y) held at equilibrium at that velocity, the
+    medium n_s in between, periodic along y; G = 0, fluid 2 dissolved only.
+    Returns u_y(x) (Eq. 7)."""
+    nx = H + 1
+    res = {0: (1, 1.0, 0.01, (0.0, 0.0, 0.0)), 1: (1, 1.0, 0.01, (0.0, U0, 0.0))}
+    p = oracle.Params(nx, 4, 1, tau=(1.0, 1.0), G=0.0, reservoirs=res)
+    ns_f = np.full((1, 4, nx), ns)
+    ns_f[..., 0] = ns_f[..., H] = 0.0
+    s = oracle.Sim(p, ns_f)
+    s.init_equilibrium(np.full((1, 4, nx), 1.0), np.full((1, 4, nx), 0.01))
+    s.step(steps)
+    return s.fields()["u"][1, 0, 0, :]
+
+
+def test_couette_without_medium_is_linear():
+    """n_s = 0: the steady Couette profile between the velocity cells is the
+    straight line U0 x / H (to the decay of the slowest transient mode,
+    exp(-nu (pi/H)^2 t) ~ 2e-6 after 20000 steps)."""
+    H, U0 = 50, 0.01
+    u = _couette_profile(0.0, 20000)
+    x = np.arange(H + 1)
+    assert np.abs(u - U0 * x / H).max() <= 1e-5 * U0
+    assert abs(u[0]) <= 1e-15 and abs(u[H] - U0) <= 1e-15
+
+
+@pytest.mark.parametrize("ns", [0.001, 0.01, 0.1, 0.5, 0.9])
+def test_couette_brinkman_profile_eq14(ns):
+    """Eq. 14: u = U0 sinh(r x) / sinh(r H), r = sqrt(2 n_s / nu).  The paper
+    reports agreement in the Brinkman regime and deviations next to the
+    moving boundary for larger n_s; held here to 3 % of U0 everywhere and
+    0.5 % of U0 for x <= 0.9 H."""
+    H, U0, nu = 50, 0.01, 1.0 / 6.0
+    u = _couette_profile(ns, 20000 if ns < 0.005 else 6000)
+    x = np.arange(H + 1)
+    r = math.sqrt(2 * ns / nu)
+    ua = U0 * np.sinh(r * x) / math.sinh(r * H)
+    err = np.abs(u - ua)
+    assert err.max() <= 0.03 * U0, err.max() / U0
+    assert err[x <= 0.9 * H].max() <= 0.005 * U0
