@@ -76,13 +76,17 @@ typedef struct {
                         storages (populations are kept as f_i - w_i rho0);
                         ignored for LBM_STORAGE_F32.  All arithmetic is
                         float32 whatever the storage.                       */
+  int32_t ns_per_component; /* 1: the workspace holds a bounce-back fraction
+                        per component, n_s,1 and n_s,2 (Eq. 1; membranes and
+                        porous obstacles, Secs. 3.5 and 4), set with
+                        lbm_set_geometry_per_component; 0: one n_s for both */
 } lbm_params;
 
 /* Observables of the current state (Sec. 4, Eqs. 18-19, Eq. A.6). */
 typedef struct {
   double mass[2];    /* sum over all nodes of rho_1 and rho_2               */
   double sat1;       /* S_1 of Eq. 19: nodes outside every reservoir, each
-                        weighted by 1 - n_s, counted when rho_1 >= 0.5;
+                        weighted by 1 - n_s,1, counted when rho_1 >= 0.5;
                         NaN when that weight sums to zero                   */
   double p_face[6];  /* mean pressure (Eq. A.6) over each reservoir face's
                         layers, faces -x,+x,-y,+y,-z,+z; NaN if no reservoir.
@@ -117,6 +121,18 @@ LBM_API void lbm_destroy(lbm_ctx *ctx);
  * EINVAL if any n_s is outside [0, 1] or not finite. */
 LBM_API lbm_status lbm_set_geometry(lbm_ctx *ctx, const float *ns, const float *gads2);
 
+/* Static geometry with a bounce-back fraction per component (Eq. 1 with
+ * n_s,sigma; the adhesion indicator of Eq. 4 is s = n_s,sigma and Eq. 7
+ * weights each component by 1 - n_s,sigma): ns1[N], ns2[N] in [0, 1],
+ * gads2[N] as for lbm_set_geometry.  ns2 = NULL means n_s,2 = n_s,1.  The
+ * context must have been created with ns_per_component = 1 when ns2 is not
+ * NULL (EINVAL otherwise); such a context also accepts lbm_set_geometry,
+ * which sets both fractions to ns.  A membrane that only fluid 1 may cross is
+ * n_s,1 = 0, n_s,2 = 1 (Sec. 4).  Host arrays, copied to the device. */
+LBM_API lbm_status lbm_set_geometry_per_component(lbm_ctx *ctx, const float *ns1,
+                                                  const float *ns2,
+                                                  const float *gads2);
+
 /* Start from rest: f_i,sigma = f^eq_i(rho_sigma, u = 0) (Eq. A.3), time 0.
  * rho_a, rho_b: host [N], each > 0 and finite (EINVAL otherwise). */
 LBM_API lbm_status lbm_init_equilibrium(lbm_ctx *ctx, const float *rho_a,
@@ -139,6 +155,16 @@ LBM_API lbm_status lbm_get_populations(lbm_ctx *ctx, float *f);
  * if the layers exceed the axis length or a density is not positive. */
 LBM_API lbm_status lbm_set_bc(lbm_ctx *ctx, int face, int layers, double rho_a,
                       double rho_b);
+
+/* Velocity boundary cells on one face (the Couette flow of Sec. 3.1): like
+ * lbm_set_bc, but the layers hold f^eq(rho_a / rho_b, u) of Eq. A.3 with the
+ * prescribed velocity u = (ux, uy, uz) for both components, evaluated in
+ * float32 with each operation rounded separately.  u = 0 is a density
+ * reservoir.  EINVAL as for lbm_set_bc, or if a velocity component is not
+ * finite or |u_d| >= 0.5. */
+LBM_API lbm_status lbm_set_bc_velocity(lbm_ctx *ctx, int face, int layers,
+                                       double rho_a, double rho_b, double ux,
+                                       double uy, double uz);
 
 /* Advance n_steps time steps (Eq. 1 plus the reservoirs), asynchronously on
  * the context's stream.  Each step launches the density pass and the fused

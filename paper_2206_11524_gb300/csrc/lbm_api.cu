@@ -85,6 +85,9 @@ bool params_valid(const lbm_params *p, const char **why) {
   for (int s = 0; s < 2; ++s)
     if (!(p->tau[s] > 0.5) || !std::isfinite(p->tau[s])) { *why = "tau must be finite and > 1/2"; return false; }
   if (!std::isfinite(p->G)) { *why = "G must be finite"; return false; }
+  if (p->ns_per_component != 0 && p->ns_per_component != 1) {
+    *why = "ns_per_component must be 0 or 1"; return false;
+  }
   for (int d = 0; d < 3; ++d)
     if (!std::isfinite(p->F_ext[d])) { *why = "F_ext must be finite"; return false; }
   return true;
@@ -171,7 +174,7 @@ struct CkptHeader {
   int64_t t, ntiles;
   hmcsc::Reservoirs applied;  // reservoirs whose reset ended step t
 };
-const char kMagic[8] = {'H', 'M', 'C', 'S', 'C', 'L', 'B', '3'};
+const char kMagic[8] = {'H', 'M', 'C', 'S', 'C', 'L', 'B', '4'};
 
 lbm_status sync_stream(lbm_ctx *c, const char *what) {
   cudaError_t e = cudaStreamSynchronize(c->stream);
@@ -195,7 +198,8 @@ size_t lbm_workspace_bytes(const lbm_params *params) {
   const char *why = nullptr;
   if (!params_valid(params, &why)) return 0;
   return hmcsc::workspace_bytes(params->nx, params->ny, params->nz,
-                                params->storage, nullptr, nullptr);
+                                params->storage, params->ns_per_component != 0,
+                                nullptr, nullptr);
 }
 
 lbm_status lbm_create(const lbm_params *params, void *d_workspace,
@@ -207,14 +211,16 @@ lbm_status lbm_create(const lbm_params *params, void *d_workspace,
   if (!params_valid(params, &why)) return LBM_EINVAL;
   if (!d_workspace || ((uintptr_t)d_workspace & 255u)) return LBM_EINVAL;
   const size_t need = hmcsc::workspace_bytes(params->nx, params->ny, params->nz,
-                                             params->storage, nullptr, nullptr);
+                                             params->storage,
+                                             params->ns_per_component != 0,
+                                             nullptr, nullptr);
   if (workspace_bytes < need) return LBM_ENOMEM;
   lbm_ctx *c = new lbm_ctx();
   c->params = *params;
   c->stream = (cudaStream_t)cuda_stream;
   c->N = (long long)params->nx * params->ny * params->nz;
   hmcsc::workspace_bytes(params->nx, params->ny, params->nz, params->storage,
-                         &c->ws, (char *)d_workspace);
+                         params->ns_per_component != 0, &c->ws, (char *)d_workspace);
   hmcsc::StepParams &sp = c->sp;
   sp.nx = params->nx;
   sp.ny = params->ny;
@@ -261,18 +267,26 @@ lbm_status lbm_create(const lbm_params *params, void *d_workspace,
 
 void lbm_destroy(lbm_ctx *ctx) { delete ctx; }
 
-lbm_status lbm_set_geometry(lbm_ctx *c, const float *ns, const float *gads2) {
+lbm_status lbm_set_geometry_per_component(lbm_ctx *c, const float *ns1,
+                                          const float *ns2, const float *gads2) {
   if (!c) return LBM_EINVAL;
-  if (!ns) return fail(c, LBM_EINVAL, "ns is NULL");
-  for (long long n = 0; n < c->N; ++n)
-    if (!(ns[n] >= 0.0f && ns[n] <= 1.0f))
-      return fail(c, LBM_EINVAL, "ns[%lld] = %g is outside [0, 1]", n, (double)ns[n]);
+  if (!ns1) return fail(c, LBM_EINVAL, "ns is NULL");
+  if (ns2 && !c->ws.ns2)
+    return fail(c, LBM_EINVAL,
+                "per-component n_s needs a context created with ns_per_component = 1");
+  const float *fields[2] = {ns1, ns2};
+  for (int k = 0; k < 2; ++k)
+    if (fields[k])
+      for (long long n = 0; n < c->N; ++n)
+        if (!(fields[k][n] >= 0.0f && fields[k][n] <= 1.0f))
+          return fail(c, LBM_EINVAL, "n_s,%d[%lld] = %g is outside [0, 1]", k + 1, n,
+                      (double)fields[k][n]);
   if (gads2)
     for (long long n = 0; n < c->N; ++n)
       if (!std::isfinite(gads2[n]))
         return fail(c, LBM_EINVAL, "gads2[%lld] is not finite", n);
   const size_t L = lin_stride(c);
-  lbm_status st = upload(c, c->ws.stage, ns, (size_t)c->N);
+  lbm_status st = upload(c, c->ws.stage, ns1, (size_t)c->N);
   if (st) return st;
   if (gads2) {
     st = upload(c, c->ws.stage + L, gads2, (size_t)c->N);
@@ -281,14 +295,23 @@ lbm_status lbm_set_geometry(lbm_ctx *c, const float *ns, const float *gads2) {
     cudaError_t e = cudaMemsetAsync(c->ws.stage + L, 0, sizeof(float) * c->N, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "memset");
   }
-  cudaError_t e = hmcsc::launch_geometry(c->sp, c->ws, c->ws.stage, c->ws.stage + L,
-                                         c->stream);
+  if (ns2) {
+    st = upload(c, c->ws.stage + 2 * L, ns2, (size_t)c->N);
+    if (st) return st;
+  }
+  cudaError_t e = hmcsc::launch_geometry(c->sp, c->ws, c->ws.stage,
+                                         ns2 ? c->ws.stage + 2 * L : nullptr,
+                                         c->ws.stage + L, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "geometry kernel");
   st = sync_stream(c, "set_geometry");
   if (st) return st;
   c->have_geometry = true;
   c->rho_at = -1;
   return LBM_OK;
+}
+
+lbm_status lbm_set_geometry(lbm_ctx *c, const float *ns, const float *gads2) {
+  return lbm_set_geometry_per_component(c, ns, nullptr, gads2);
 }
 
 lbm_status lbm_init_equilibrium(lbm_ctx *c, const float *rho_a,
@@ -412,18 +435,27 @@ lbm_status lbm_get_populations(lbm_ctx *c, float *f) {
                          stored_ref(c, rho_enc.data(), s, i, x, y, z));
             }
             if (c->sp.res.any) {
-              // a node inside a reservoir holds w_i rho_res (see the kernels)
+              // a node inside a reservoir holds its prescribed equilibrium
+              // (see the kernels)
               const int face = reservoir_face(c->sp.res, c->params, x, y, z);
-              if (face >= 0) v = hmcsc::wgt(i) * c->sp.res.rho[face][s];
+              if (face >= 0) {
+                const hmcsc::Reservoirs &r = c->sp.res;
+                v = r.moving ? hmcsc::res_feq(i, r.rho[face][s], r.u[face][0],
+                                              r.u[face][1], r.u[face][2])
+                             : hmcsc::wgt(i) * r.rho[face][s];
+              }
             }
             f[((size_t)s * kQ + i) * N + n] = v;
           }
   return LBM_OK;
 }
 
-lbm_status lbm_set_bc(lbm_ctx *c, int face, int layers, double rho_a,
-                      double rho_b) {
+lbm_status lbm_set_bc_velocity(lbm_ctx *c, int face, int layers, double rho_a,
+                               double rho_b, double ux, double uy, double uz) {
   if (!c) return LBM_EINVAL;
+  if (!std::isfinite(ux) || !std::isfinite(uy) || !std::isfinite(uz) ||
+      std::fabs(ux) >= 0.5 || std::fabs(uy) >= 0.5 || std::fabs(uz) >= 0.5)
+    return fail(c, LBM_EINVAL, "boundary velocity must be finite and below 0.5");
   if (face < 0 || face >= kFaces) return fail(c, LBM_EINVAL, "face must be 0..5");
   const int len = face < 2 ? c->params.nx : (face < 4 ? c->params.ny : c->params.nz);
   if (layers < 0 || layers > len) return fail(c, LBM_EINVAL, "layers out of range");
@@ -435,10 +467,22 @@ lbm_status lbm_set_bc(lbm_ctx *c, int face, int layers, double rho_a,
   r.layers[face] = layers;
   r.rho[face][0] = layers > 0 ? (float)rho_a : 0.0f;
   r.rho[face][1] = layers > 0 ? (float)rho_b : 0.0f;
-  int any = 0;
-  for (int k = 0; k < kFaces; ++k) any |= r.layers[k] > 0;
+  r.u[face][0] = layers > 0 ? (float)ux : 0.0f;
+  r.u[face][1] = layers > 0 ? (float)uy : 0.0f;
+  r.u[face][2] = layers > 0 ? (float)uz : 0.0f;
+  int any = 0, moving = 0;
+  for (int k = 0; k < kFaces; ++k) {
+    any |= r.layers[k] > 0;
+    moving |= r.layers[k] > 0 && (r.u[k][0] != 0.0f || r.u[k][1] != 0.0f || r.u[k][2] != 0.0f);
+  }
   r.any = any;
+  r.moving = moving;
   return LBM_OK;
+}
+
+lbm_status lbm_set_bc(lbm_ctx *c, int face, int layers, double rho_a,
+                      double rho_b) {
+  return lbm_set_bc_velocity(c, face, layers, rho_a, rho_b, 0.0, 0.0, 0.0);
 }
 
 lbm_status lbm_density(lbm_ctx *c) {
@@ -599,7 +643,7 @@ lbm_status lbm_save(lbm_ctx *c, void *host_buf, size_t bytes) {
   CkptHeader h;
   memset(&h, 0, sizeof h);
   memcpy(h.magic, kMagic, 8);
-  h.version = 3;
+  h.version = 4;
   h.storage = c->params.storage;
   h.nx = c->params.nx;
   h.ny = c->params.ny;
@@ -626,7 +670,7 @@ lbm_status lbm_load(lbm_ctx *c, const void *host_buf, size_t bytes) {
     return fail(c, LBM_EINVAL, "checkpoint buffer too small");
   CkptHeader h;
   memcpy(&h, host_buf, sizeof h);
-  if (memcmp(h.magic, kMagic, 8) != 0 || h.version != 3)
+  if (memcmp(h.magic, kMagic, 8) != 0 || h.version != 4)
     return fail(c, LBM_EINVAL, "not a checkpoint of this library");
   if (h.nx != c->params.nx || h.ny != c->params.ny || h.nz != c->params.nz ||
       h.storage != c->params.storage || h.ntiles != c->sp.ntiles || h.t < 0)
@@ -661,6 +705,7 @@ lbm_status batch_check(lbm_ctx *const *ctxs, int n) {
     if (!ctxs[k]) return LBM_EINVAL;
     if (!ctxs[k]->have_geometry || !ctxs[k]->have_state) return LBM_ESTATE;
     if (ctxs[k]->sp.storage != ctxs[0]->sp.storage) return LBM_EINVAL;
+    if ((ctxs[k]->ws.ns2 != nullptr) != (ctxs[0]->ws.ns2 != nullptr)) return LBM_EINVAL;
     for (int j = 0; j < k; ++j)
       if (ctxs[j] == ctxs[k]) return LBM_EINVAL;
   }

@@ -139,16 +139,21 @@ __device__ __forceinline__ void first_moment(const float (&v)[kQ],
 // Total force per unit mass of each component, F_tot,sigma / rho_sigma
 // (Eqs. 3-5; rho_sigma cancels against the prefactor of Eqs. 3-4 and the
 // density ratio of Eq. 5, so no division by a vanishing component density):
-//   g_1 = -G S_2 + A + F_ext / rho,   g_2 = -G S_1 - A + F_ext / rho
-// with S_sigma = sum_i w_i rho_sigma(x + c_i) c_i and A = sum_i w_i a(x + c_i)
-// c_i, a = G_ads,2 n_s (G_ads,1 = -G_ads,2, Table 1).  Opposite directions
-// are summed as pairs, so a uniform field gives exactly zero.
+//   g_1 = -G S_2 + A_1 + F_ext / rho,   g_2 = -G S_1 - A_2 + F_ext / rho
+// with S_sigma = sum_i w_i rho_sigma(x + c_i) c_i and A_sigma = sum_i w_i
+// a_sigma(x + c_i) c_i, a_sigma = G_ads,2 n_s,sigma (G_ads,1 = -G_ads,2,
+// Table 1; the indicator of Eq. 4 is the component's own fraction).  With
+// one fraction for both (PC = false) A_1 = A_2.  Opposite directions are
+// summed as pairs, so a uniform field gives exactly zero.
+template <bool PC>
 __device__ __forceinline__ void force_per_mass(const StepParams &p,
                                                const float2 *__restrict__ rho,
                                                const float *__restrict__ ads,
+                                               const float *__restrict__ ads2,
                                                const Geo &g, float rho_tot,
                                                float (&g1)[3], float (&g2)[3]) {
-  float s1[3] = {0.f, 0.f, 0.f}, s2[3] = {0.f, 0.f, 0.f}, sa[3] = {0.f, 0.f, 0.f};
+  float s1[3] = {0.f, 0.f, 0.f}, s2[3] = {0.f, 0.f, 0.f};
+  float sa[3] = {0.f, 0.f, 0.f}, sb[3] = {0.f, 0.f, 0.f};
 #pragma unroll
   for (int i = 1; i <= 9; ++i) {
     const int mp = g.node(cx(i), cy(i), cz(i));
@@ -160,16 +165,18 @@ __device__ __forceinline__ void force_per_mass(const StepParams &p,
     const float d1 = wgt(i) * (rp.x - rm.x);
     const float d2 = wgt(i) * (rp.y - rm.y);
     const float da = wgt(i) * (ap - am);
-    if (cx(i)) { s1[0] += cx(i) > 0 ? d1 : -d1; s2[0] += cx(i) > 0 ? d2 : -d2; sa[0] += cx(i) > 0 ? da : -da; }
-    if (cy(i)) { s1[1] += cy(i) > 0 ? d1 : -d1; s2[1] += cy(i) > 0 ? d2 : -d2; sa[1] += cy(i) > 0 ? da : -da; }
-    if (cz(i)) { s1[2] += cz(i) > 0 ? d1 : -d1; s2[2] += cz(i) > 0 ? d2 : -d2; sa[2] += cz(i) > 0 ? da : -da; }
+    float db = 0.0f;
+    if (PC) db = wgt(i) * (__ldg(&ads2[mp]) - __ldg(&ads2[mm]));
+    if (cx(i)) { s1[0] += cx(i) > 0 ? d1 : -d1; s2[0] += cx(i) > 0 ? d2 : -d2; sa[0] += cx(i) > 0 ? da : -da; if (PC) sb[0] += cx(i) > 0 ? db : -db; }
+    if (cy(i)) { s1[1] += cy(i) > 0 ? d1 : -d1; s2[1] += cy(i) > 0 ? d2 : -d2; sa[1] += cy(i) > 0 ? da : -da; if (PC) sb[1] += cy(i) > 0 ? db : -db; }
+    if (cz(i)) { s1[2] += cz(i) > 0 ? d1 : -d1; s2[2] += cz(i) > 0 ? d2 : -d2; sa[2] += cz(i) > 0 ? da : -da; if (PC) sb[2] += cz(i) > 0 ? db : -db; }
   }
   const float inv_rho = 1.0f / rho_tot;
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     const float fe = p.F[d] * inv_rho;
     g1[d] = -p.G * s2[d] + sa[d] + fe;
-    g2[d] = -p.G * s1[d] - sa[d] + fe;
+    g2[d] = -p.G * s1[d] - (PC ? sb[d] : sa[d]) + fe;
   }
 }
 
@@ -207,8 +214,17 @@ __device__ __forceinline__ bool box_in_reservoir(const StepParams &p, int xlo,
          (L[4] && zlo < L[4]) || (L[5] && zhi >= p.nz - L[5]);
 }
 
-// A node inside a reservoir holds the prescribed equilibrium at rest.  Only
-// blocks whose box meets a reservoir (`maybe`, block-uniform) look.
+// Prescribed velocity component d of face `face` (selects).
+__device__ __forceinline__ float res_u(const StepParams &p, int face, int d) {
+  float u = p.res.u[0][d];
+#pragma unroll
+  for (int k = 1; k < kFaces; ++k) u = face == k ? p.res.u[k][d] : u;
+  return u;
+}
+
+// A node inside a reservoir holds the prescribed equilibrium: at rest for a
+// density reservoir, at the face's velocity for velocity boundary cells.
+// Only blocks whose box meets a reservoir (`maybe`, block-uniform) look.
 __device__ __forceinline__ void reservoir_state(const StepParams &p, bool maybe,
                                                 int x, int y, int z,
                                                 float (&v1)[kQ], float (&v2)[kQ]) {
@@ -216,10 +232,19 @@ __device__ __forceinline__ void reservoir_state(const StepParams &p, bool maybe,
   const int face = res_face(p, x, y, z);
   if (face >= 0) {
     const float r1 = res_rho(p, face, 0), r2 = res_rho(p, face, 1);
+    if (p.res.moving) {
+      const float ux = res_u(p, face, 0), uy = res_u(p, face, 1), uz = res_u(p, face, 2);
 #pragma unroll
-    for (int i = 0; i < kQ; ++i) {
-      v1[i] = wgt(i) * r1;
-      v2[i] = wgt(i) * r2;
+      for (int i = 0; i < kQ; ++i) {
+        v1[i] = res_feq(i, r1, ux, uy, uz);
+        v2[i] = res_feq(i, r2, ux, uy, uz);
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < kQ; ++i) {
+        v1[i] = wgt(i) * r1;
+        v2[i] = wgt(i) * r2;
+      }
     }
   }
 }
@@ -268,8 +293,9 @@ __device__ __forceinline__ void put2(const StepParams &p, const Workspace &w,
 // equilibrium: B_i = b f^eq_i = (b w_i rho_s)[1 - 1.5 u.u + 4.5 (c_i.u)^2
 // +- 3 c_i.u], so each population costs two fused multiply-adds on top of B_i.
 struct Relax {
-  float a, base, br, br18, br36, moving;
-  __device__ __forceinline__ Relax(float om, float nsx, float rho_s, const float (&u)[3]) {
+  float a, base, br, br18, br36, moving, nsx;
+  __device__ __forceinline__ Relax(float om, float ns_s, float rho_s, const float (&u)[3]) {
+    nsx = ns_s;
     a = (1.0f - nsx) * (1.0f - om);
     const float b = (1.0f - nsx) * om;
     base = 1.0f - 1.5f * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
@@ -280,7 +306,7 @@ struct Relax {
   }
   // post-collision values of the opposite pair (i, i + 9)
   __device__ __forceinline__ void pair(int i, const float (&u)[3], const float (&v)[kQ],
-                                       float nsx, float &out_i, float &out_j) {
+                                       float &out_i, float &out_j) {
     const int j = i + 9;
     const float cu = cx(i) * u[0] + cy(i) * u[1] + cz(i) * u[2];
     const float bw = wgt(i) == (1.0f / 18.0f) ? br18 : br36;
@@ -292,7 +318,7 @@ struct Relax {
     out_j = fmaf(a, v[j], fmaf(nsx, v[i], B_j));
   }
   // post-collision rest population: B_0 = b rho_s - sum of the moving B_i
-  __device__ __forceinline__ float rest(const float (&v)[kQ], float nsx) const {
+  __device__ __forceinline__ float rest(const float (&v)[kQ]) const {
     return fmaf(a + nsx, v[0], br - moving);
   }
 };
@@ -302,20 +328,21 @@ __device__ __forceinline__ void collide_put2(const StepParams &p, const Workspac
                                              const Geo &g, const float (&v1)[kQ],
                                              const float (&v2)[kQ], float r1,
                                              float r2, const float (&u1)[3],
-                                             const float (&u2)[3], float nsx) {
-  Relax c1(p.omega[0], nsx, r1, u1), c2(p.omega[1], nsx, r2, u2);
+                                             const float (&u2)[3], float ns1,
+                                             float ns2) {
+  Relax c1(p.omega[0], ns1, r1, u1), c2(p.omega[1], ns2, r2, u2);
 #pragma unroll
   for (int i = 1; i <= 9; ++i) {
     float o1i, o1j, o2i, o2j;
-    c1.pair(i, u1, v1, nsx, o1i, o1j);
-    c2.pair(i, u2, v2, nsx, o2i, o2j);
+    c1.pair(i, u1, v1, o1i, o1j);
+    c2.pair(i, u2, v2, o2i, o2j);
     put2<PARITY, ST>(p, w, g, i, o1i, o2i, r1, r2);
     put2<PARITY, ST>(p, w, g, i + 9, o1j, o2j, r1, r2);
   }
-  put2<PARITY, ST>(p, w, g, 0, c1.rest(v1, nsx), c2.rest(v2, nsx), r1, r2);
+  put2<PARITY, ST>(p, w, g, 0, c1.rest(v1), c2.rest(v2), r1, r2);
 }
 
-template <int PARITY, int ST>
+template <int PARITY, int ST, bool PC>
 __device__ __forceinline__ void collide_body(const StepParams &p,
                                              const Workspace &w, bool maybe_res,
                                              int x, int y, int z) {
@@ -329,7 +356,7 @@ __device__ __forceinline__ void collide_body(const StepParams &p,
   first_moment(f2, j2);
 
   float g1[3], g2[3];
-  force_per_mass(p, w.rho, w.ads, g, r1 + r2, g1, g2);
+  force_per_mass<PC>(p, w.rho, w.ads, w.ads2, g, r1 + r2, g1, g2);
 
   // Eq. 6: common velocity sum_s j_s/tau_s / sum_s rho_s/tau_s, then the
   // Shan-Chen shift tau_s F_tot,s / rho_s = tau_s g_s.
@@ -342,8 +369,9 @@ __device__ __forceinline__ void collide_body(const StepParams &p,
     u2[d] = uc + p.tau[1] * g2[d];
   }
 
-  const float nsx = w.ns[g.node(0, 0, 0)];
-  collide_put2<PARITY, ST>(p, w, g, f1, f2, r1, r2, u1, u2, nsx);
+  const float ns1 = w.ns[g.node(0, 0, 0)];
+  const float ns2 = PC ? w.ns2[g.node(0, 0, 0)] : ns1;
+  collide_put2<PARITY, ST>(p, w, g, f1, f2, r1, r2, u1, u2, ns1, ns2);
 }
 
 
@@ -413,7 +441,7 @@ __global__ void __launch_bounds__(DensityShape<CFG>::threads)
   w.rho[g.node(0, 0, 0)] = make_float2(sum19(v1), sum19(v2));
 }
 
-template <int PARITY, int ST, int CFG>
+template <int PARITY, int ST, int CFG, bool PC>
 __global__ void __launch_bounds__(CollideShape<PARITY, ST, CFG>::threads,
                                   CollideShape<PARITY, ST, CFG>::s.minb)
     k_collide_stream(StepParams p, Workspace w) {
@@ -422,12 +450,12 @@ __global__ void __launch_bounds__(CollideShape<PARITY, ST, CFG>::threads,
   block_coords<S.by, S.bz>(x, y, z);
   const bool maybe_res = block_in_reservoir<S.by, S.bz>(p);
   if (x >= p.nx || y >= p.ny || z >= p.nz) return;
-  collide_body<PARITY, ST>(p, w, maybe_res, x, y, z);
+  collide_body<PARITY, ST, PC>(p, w, maybe_res, x, y, z);
 }
 
 // Macroscopic fields of the current state into the linear staging planes:
 // rho_1, rho_2, u_macro (Eq. 7) x, y, z, p (Eq. A.6).
-template <int PARITY, int ST>
+template <int PARITY, int ST, bool PC>
 __global__ void __launch_bounds__(kTile * kFieldsBY * kFieldsBZ)
     k_fields(StepParams p, Workspace w) {
   int x, y, z;
@@ -444,16 +472,23 @@ __global__ void __launch_bounds__(kTile * kFieldsBY * kFieldsBZ)
   first_moment(f2, j2);
   float g1[3], g2[3];
   const float rho = r1 + r2;
-  force_per_mass(p, w.rho, w.ads, g, rho, g1, g2);
+  force_per_mass<PC>(p, w.rho, w.ads, w.ads2, g, rho, g1, g2);
   const float fluid = 1.0f - w.ns[g.node(0, 0, 0)];
+  const float fluid2 = PC ? 1.0f - w.ns2[g.node(0, 0, 0)] : fluid;
   const long long L = p.nlin;
   const long long n = x + (long long)p.nx * (y + (long long)p.ny * z);
   w.stage[n] = r1;
   w.stage[L + n] = r2;
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
-    const float m = (j1[d] + 0.5f * r1 * g1[d]) + (j2[d] + 0.5f * r2 * g2[d]);
-    w.stage[(2 + d) * L + n] = fluid * m / rho;
+    if (PC) {
+      const float m = fluid * (j1[d] + 0.5f * r1 * g1[d]) +
+                      fluid2 * (j2[d] + 0.5f * r2 * g2[d]);
+      w.stage[(2 + d) * L + n] = m / rho;
+    } else {
+      const float m = (j1[d] + 0.5f * r1 * g1[d]) + (j2[d] + 0.5f * r2 * g2[d]);
+      w.stage[(2 + d) * L + n] = fluid * m / rho;
+    }
   }
   w.stage[5 * L + n] = (rho + p.G * r1 * r2) * (1.0f / 3.0f);
 }
@@ -535,7 +570,8 @@ __global__ void __launch_bounds__(kTile * kBatchBY)
   it.w.rho[g.node(0, 0, 0)] = make_float2(sum19(v1), sum19(v2));
 }
 
-template <int ST>
+// All items of one launch have per-component fractions (PC) or none do.
+template <int ST, bool PC>
 __global__ void __launch_bounds__(kTile * kBatchBY, CollideShape<1, ST, 0>::s.minb)
     k_batch_collide(const __grid_constant__ BatchArgs a) {
   int r, x, y, z;
@@ -543,9 +579,9 @@ __global__ void __launch_bounds__(kTile * kBatchBY, CollideShape<1, ST, 0>::s.mi
   if (!batch_coords(a, r, x, y, z, maybe_res)) return;
   const BatchItem &it = a.item[r];
   if (it.parity == 0)
-    collide_body<0, ST>(it.p, it.w, maybe_res, x, y, z);
+    collide_body<0, ST, PC>(it.p, it.w, maybe_res, x, y, z);
   else
-    collide_body<1, ST>(it.p, it.w, maybe_res, x, y, z);
+    collide_body<1, ST, PC>(it.p, it.w, maybe_res, x, y, z);
 }
 
 }  // namespace

@@ -106,13 +106,47 @@ __host__ __device__ constexpr float wgt(int i) {
                                                                        : (1.0f / 36.0f));
 }
 
-// Reservoir description handed to kernels: layers per face (0 = none) and
-// the prescribed densities.  Faces -x,+x,-y,+y,-z,+z; higher index wins.
+// Reservoir description handed to kernels: layers per face (0 = none), the
+// prescribed densities and velocity (zero for a density reservoir; the
+// velocity boundary cells of the Couette flow otherwise).  Faces
+// -x,+x,-y,+y,-z,+z; higher index wins.
 struct Reservoirs {
   int layers[kFaces];
   float rho[kFaces][2];
+  float u[kFaces][3];
   int any;
+  int moving;  // some face has a nonzero velocity
 };
+
+// Float products and sums rounded one by one (no fused multiply-add on the
+// device; the host side is compiled without contraction), so that device
+// and host evaluate res_feq identically.
+__host__ __device__ inline float mul_rn(float a, float b) {
+#ifdef __CUDA_ARCH__
+  return __fmul_rn(a, b);
+#else
+  return a * b;
+#endif
+}
+__host__ __device__ inline float add_rn(float a, float b) {
+#ifdef __CUDA_ARCH__
+  return __fadd_rn(a, b);
+#else
+  return a + b;
+#endif
+}
+
+// f^eq_i(rho, u) of Eq. A.3 (c_s^2 = 1/3) for a node held at a prescribed
+// state, with every operation rounded on its own.
+__host__ __device__ inline float res_feq(int i, float rho, float ux, float uy,
+                                         float uz) {
+  const float cu = add_rn(add_rn(cx(i) * ux, cy(i) * uy), cz(i) * uz);
+  const float uu = add_rn(add_rn(mul_rn(ux, ux), mul_rn(uy, uy)), mul_rn(uz, uz));
+  float poly = add_rn(1.0f, mul_rn(3.0f, cu));
+  poly = add_rn(poly, mul_rn(4.5f, mul_rn(cu, cu)));
+  poly = add_rn(poly, -mul_rn(1.5f, uu));
+  return mul_rn(mul_rn(wgt(i), rho), poly);
+}
 
 // Per-launch constants.  `res` lists the reservoirs whose reset ended the
 // previous step; kernels read a node inside one of them as its equilibrium.
@@ -138,8 +172,12 @@ struct Workspace {
   float2 *rho_enc;   // [ntiles * 32] *_LOCAL storages: each node's density of
                      // the previous step, which its stored populations are
                      // offset from
-  float *ns;         // [ntiles * 32] bounce-back fraction n_s
-  float *ads;        // [ntiles * 32] a = G_ads,2 * n_s (adhesion stencil source)
+  float *ns;         // [ntiles * 32] bounce-back fraction n_s (n_s,1 when the
+                     // fractions are per component)
+  float *ads;        // [ntiles * 32] a = G_ads,2 * n_s (adhesion stencil source;
+                     // G_ads,2 n_s,1 when per component)
+  float *ns2;        // [ntiles * 32] n_s,2, or nullptr: one fraction for both
+  float *ads2;       // [ntiles * 32] G_ads,2 * n_s,2, or nullptr
   float *stage;      // [6][nlin] linear (x fastest) staging for host transfers
   double *red;       // [kRedBlocks][kRedK] partial sums + [kRedK] result
 };
@@ -160,8 +198,10 @@ __host__ __device__ inline Tiling tiling(long long nx, long long ny, long long n
   return t;
 }
 
+// per_component: room for n_s,2 and its adhesion source (Eq. 1 with a
+// bounce-back fraction per component).
 size_t workspace_bytes(long long nx, long long ny, long long nz, int storage,
-                       Workspace *out, char *base);
+                       bool per_component, Workspace *out, char *base);
 
 // Several lattices advanced by one launch per pass: block b of the grid
 // belongs to item r with prefix[r] <= b < prefix[r + 1]; an item's blocks
@@ -180,6 +220,7 @@ struct BatchArgs {
   int prefix[kBatchMax + 1];
   BatchItem item[kBatchMax];
 };
+static_assert(sizeof(BatchArgs) <= 32000, "kernel parameter limit");
 cudaError_t launch_batch_density(const BatchArgs &a, int storage, cudaStream_t s);
 cudaError_t launch_batch_collide(const BatchArgs &a, int storage, cudaStream_t s);
 
@@ -205,9 +246,11 @@ HMCSC_DECLARE_STORAGE_LAUNCHERS(bf16l)
 cudaError_t launch_init_equilibrium(const StepParams &p, const Workspace &w,
                                     const float *rho_a, const float *rho_b,
                                     cudaStream_t s);
+// ns2_lin may be nullptr (n_s,2 = n_s,1); it is read only when the
+// workspace holds per-component fractions.
 cudaError_t launch_geometry(const StepParams &p, const Workspace &w,
-                            const float *ns_lin, const float *gads2_lin,
-                            cudaStream_t s);
+                            const float *ns_lin, const float *ns2_lin,
+                            const float *gads2_lin, cudaStream_t s);
 // `cfg` selects the launch shape of the pass (0 = default; see
 // density_shape / collide_shape in lbm_device.cuh).
 constexpr int kDensityConfigs = 3, kCollideConfigs = 4;

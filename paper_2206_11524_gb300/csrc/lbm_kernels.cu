@@ -14,17 +14,25 @@ __device__ __forceinline__ long long tiled_of_linear(const StepParams &p,
   return (yz * p.ntx + x / kTile) * kTile + x % kTile;
 }
 
-// n_s and the adhesion source a = G_ads,2 n_s in tiled order.
+// n_s and the adhesion source a = G_ads,2 n_s in tiled order (per component
+// when the workspace holds n_s,2).
 __global__ void k_geometry(StepParams p, Workspace w,
                            const float *__restrict__ ns_lin,
+                           const float *__restrict__ ns2_lin,
                            const float *__restrict__ gads2_lin) {
   const long long N = (long long)p.nx * p.ny * p.nz;
   for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
        n += (long long)gridDim.x * blockDim.x) {
     const long long tn = tiled_of_linear(p, n);
     const float s = ns_lin[n];
+    const float g = gads2_lin[n];
     w.ns[tn] = s;
-    w.ads[tn] = gads2_lin[n] * s;
+    w.ads[tn] = g * s;
+    if (w.ns2) {
+      const float s2 = ns2_lin ? ns2_lin[n] : s;
+      w.ns2[tn] = s2;
+      w.ads2[tn] = g * s2;
+    }
   }
 }
 
@@ -104,7 +112,7 @@ int flat_blocks(const StepParams &p) {
 }  // namespace
 
 size_t workspace_bytes(long long nx, long long ny, long long nz, int storage,
-                       Workspace *out, char *base) {
+                       bool per_component, Workspace *out, char *base) {
   const Tiling t = tiling(nx, ny, nz);
   const size_t nt = (size_t)t.ntiles * kTile;
   size_t off = 0;
@@ -120,6 +128,8 @@ size_t workspace_bytes(long long nx, long long ny, long long nz, int storage,
   size_t o_ads = take(sizeof(float) * nt);
   size_t o_stage = take(sizeof(float) * 6 * (size_t)t.nlin);
   size_t o_red = take(sizeof(double) * (kRedBlocks + 1) * kRedK);
+  size_t o_ns2 = take(per_component ? sizeof(float) * nt : 0);
+  size_t o_ads2 = take(per_component ? sizeof(float) * nt : 0);
   if (out) {
     out->f = (void *)(base + o_f);
     out->rho = (float2 *)(base + o_rho);
@@ -128,14 +138,16 @@ size_t workspace_bytes(long long nx, long long ny, long long nz, int storage,
     out->ads = (float *)(base + o_ads);
     out->stage = (float *)(base + o_stage);
     out->red = (double *)(base + o_red);
+    out->ns2 = per_component ? (float *)(base + o_ns2) : nullptr;
+    out->ads2 = per_component ? (float *)(base + o_ads2) : nullptr;
   }
   return off;
 }
 
 cudaError_t launch_geometry(const StepParams &p, const Workspace &w,
-                            const float *ns_lin, const float *gads2_lin,
-                            cudaStream_t s) {
-  k_geometry<<<flat_blocks(p), 256, 0, s>>>(p, w, ns_lin, gads2_lin);
+                            const float *ns_lin, const float *ns2_lin,
+                            const float *gads2_lin, cudaStream_t s) {
+  k_geometry<<<flat_blocks(p), 256, 0, s>>>(p, w, ns_lin, ns2_lin, gads2_lin);
   return cudaGetLastError();
 }
 

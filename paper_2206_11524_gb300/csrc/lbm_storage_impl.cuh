@@ -21,7 +21,10 @@ template <int PARITY, int CFG>
 void collide_cfg(const StepParams &p, const Workspace &w, cudaStream_t s) {
   constexpr Shape S = CollideShape<PARITY, kST, CFG>::s;
   const dim3 grid(p.ntx, (p.ny + S.by - 1) / S.by, (p.nz + S.bz - 1) / S.bz);
-  k_collide_stream<PARITY, kST, CFG><<<grid, dim3(kTile, S.by, S.bz), 0, s>>>(p, w);
+  if (w.ns2)
+    k_collide_stream<PARITY, kST, CFG, true><<<grid, dim3(kTile, S.by, S.bz), 0, s>>>(p, w);
+  else
+    k_collide_stream<PARITY, kST, CFG, false><<<grid, dim3(kTile, S.by, S.bz), 0, s>>>(p, w);
 }
 template <int PARITY>
 void density_any(const StepParams &p, const Workspace &w, int cfg, cudaStream_t s) {
@@ -59,8 +62,13 @@ cudaError_t HMCSC_NAME(launch_fields)(const StepParams &p, const Workspace &w,
   const dim3 grid(p.ntx, (p.ny + kFieldsBY - 1) / kFieldsBY,
                   (p.nz + kFieldsBZ - 1) / kFieldsBZ);
   const dim3 block(kTile, kFieldsBY, kFieldsBZ);
-  if (parity == 0) k_fields<0, kST><<<grid, block, 0, s>>>(p, w);
-  else k_fields<1, kST><<<grid, block, 0, s>>>(p, w);
+  if (w.ns2) {
+    if (parity == 0) k_fields<0, kST, true><<<grid, block, 0, s>>>(p, w);
+    else k_fields<1, kST, true><<<grid, block, 0, s>>>(p, w);
+  } else {
+    if (parity == 0) k_fields<0, kST, false><<<grid, block, 0, s>>>(p, w);
+    else k_fields<1, kST, false><<<grid, block, 0, s>>>(p, w);
+  }
   return cudaGetLastError();
 }
 
@@ -80,7 +88,11 @@ cudaError_t HMCSC_NAME(launch_batch_density)(const BatchArgs &a, cudaStream_t s)
 }
 
 cudaError_t HMCSC_NAME(launch_batch_collide)(const BatchArgs &a, cudaStream_t s) {
-  k_batch_collide<kST><<<(unsigned)a.prefix[a.n], dim3(kTile, kBatchBY, 1), 0, s>>>(a);
+  const dim3 grid((unsigned)a.prefix[a.n]), block(kTile, kBatchBY, 1);
+  if (a.item[0].w.ns2)
+    k_batch_collide<kST, true><<<grid, block, 0, s>>>(a);
+  else
+    k_batch_collide<kST, false><<<grid, block, 0, s>>>(a);
   return cudaGetLastError();
 }
 

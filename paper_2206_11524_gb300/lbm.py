@@ -37,6 +37,7 @@ ABI_SYMBOLS = (
     "lbm_save", "lbm_load", "lbm_last_error", "lbm_reduce_fields_noalloc",
     "lbm_batch_step", "lbm_batch_graph_create", "lbm_batch_graph_launch",
     "lbm_batch_graph_destroy", "lbm_set_launch_config",
+    "lbm_set_geometry_per_component", "lbm_set_bc_velocity",
 )
 LBM_DENSITY_CONFIGS, LBM_COLLIDE_CONFIGS = 3, 4
 LBM_BATCH_MAX = 64
@@ -46,7 +47,8 @@ class lbm_params(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
                 ("nz", ctypes.c_int32), ("storage", ctypes.c_int32),
                 ("tau", ctypes.c_double * 2), ("G", ctypes.c_double),
-                ("F_ext", ctypes.c_double * 3), ("rho0", ctypes.c_double * 2)]
+                ("F_ext", ctypes.c_double * 3), ("rho0", ctypes.c_double * 2),
+                ("ns_per_component", ctypes.c_int32)]
 
 
 class lbm_observables(ctypes.Structure):
@@ -86,10 +88,12 @@ def load(path: str | None = None):
         "lbm_create": (ctypes.c_int, [P, vp, ctypes.c_size_t, vp, ctypes.POINTER(vp)]),
         "lbm_destroy": (None, [vp]),
         "lbm_set_geometry": (ctypes.c_int, [vp, fp, fp]),
+        "lbm_set_geometry_per_component": (ctypes.c_int, [vp, fp, fp, fp]),
         "lbm_init_equilibrium": (ctypes.c_int, [vp, fp, fp]),
         "lbm_set_populations": (ctypes.c_int, [vp, fp]),
         "lbm_get_populations": (ctypes.c_int, [vp, fp]),
         "lbm_set_bc": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double]),
+        "lbm_set_bc_velocity": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int] + [ctypes.c_double] * 5),
         "lbm_step": (ctypes.c_int, [vp, ctypes.c_int]),
         "lbm_density": (ctypes.c_int, [vp]),
         "lbm_collide_stream": (ctypes.c_int, [vp]),
@@ -165,6 +169,13 @@ def lbm_set_geometry(ctx, ns, gads2=None, n=None):
     return _check(ctx, load().lbm_set_geometry(ctx, pa, pb))
 
 
+def lbm_set_geometry_per_component(ctx, ns1, ns2, gads2=None, n=None):
+    a, pa = _f32(ns1, n)
+    b, pb = _f32(ns2, n)
+    c, pc = _f32(gads2, n)
+    return _check(ctx, load().lbm_set_geometry_per_component(ctx, pa, pb, pc))
+
+
 def lbm_init_equilibrium(ctx, rho_a, rho_b, n=None):
     a, pa = _f32(rho_a, n)
     b, pb = _f32(rho_b, n)
@@ -184,6 +195,11 @@ def lbm_get_populations(ctx, out: np.ndarray):
 
 def lbm_set_bc(ctx, face, layers, rho_a, rho_b):
     return _check(ctx, load().lbm_set_bc(ctx, face, layers, rho_a, rho_b))
+
+
+def lbm_set_bc_velocity(ctx, face, layers, rho_a, rho_b, ux, uy, uz):
+    return _check(ctx, load().lbm_set_bc_velocity(ctx, face, layers, rho_a, rho_b,
+                                                  ux, uy, uz))
 
 
 def lbm_step(ctx, n_steps):
@@ -310,7 +326,8 @@ class Lattice:
     """
 
     def __init__(self, nx, ny, nz, tau=(1.0, 1.0), G=1.75, F_ext=(0, 0, 0),
-                 stream=None, device=None, storage="f32", rho0=(0.0, 0.0)):
+                 stream=None, device=None, storage="f32", rho0=(0.0, 0.0),
+                 ns_per_component=False):
         import torch
         self.shape = (nz, ny, nx)
         self.N = nx * ny * nz
@@ -323,6 +340,7 @@ class Lattice:
         p.G = G
         for d in range(3):
             p.F_ext[d] = F_ext[d]
+        p.ns_per_component = 1 if ns_per_component else 0
         self.params = p
         nbytes = lbm_workspace_bytes(p)
         if nbytes == 0:
@@ -344,8 +362,13 @@ class Lattice:
         except Exception:
             pass
 
-    def set_geometry(self, ns, gads2=None):
-        lbm_set_geometry(self.ctx, ns, gads2, self.N)
+    def set_geometry(self, ns, gads2=None, ns2=None):
+        """n_s (both components, or fluid 1 when ns2 is given), G_ads,2 and
+        optionally n_s,2 (needs ns_per_component=True)."""
+        if ns2 is None:
+            lbm_set_geometry(self.ctx, ns, gads2, self.N)
+        else:
+            lbm_set_geometry_per_component(self.ctx, ns, ns2, gads2, self.N)
 
     def init_equilibrium(self, rho_a, rho_b):
         lbm_init_equilibrium(self.ctx, rho_a, rho_b, self.N)
@@ -358,8 +381,13 @@ class Lattice:
         lbm_get_populations(self.ctx, out)
         return out
 
-    def set_bc(self, face, layers, rho_a=1.0, rho_b=1.0):
-        lbm_set_bc(self.ctx, face, layers, rho_a, rho_b)
+    def set_bc(self, face, layers, rho_a=1.0, rho_b=1.0, u=None):
+        """Density reservoir on `face` (u None), or velocity boundary cells
+        held at f^eq(rho, u)."""
+        if u is None:
+            lbm_set_bc(self.ctx, face, layers, rho_a, rho_b)
+        else:
+            lbm_set_bc_velocity(self.ctx, face, layers, rho_a, rho_b, *u)
 
     def step(self, n=1):
         lbm_step(self.ctx, n)

@@ -373,3 +373,64 @@ def test_full_size_electrode_sampled(steps):
     obs = g.observables()
     assert obs["nonfinite"] == 0
     g.close()
+
+
+def test_velocity_boundary_cells_match():
+    """Boundary cells held at a prescribed velocity on two faces (the
+    Couette boundaries of Sec. 3.1) plus a density reservoir: populations
+    after 1-3 steps and the fields."""
+    shape = (4, 10, 18)
+    ns, gads = synth.random_geometry(shape, 17)
+    res = {0: (2, 1.0, 0.05, (0.0, 0.02, -0.01)), 3: (1, 0.3, 0.6, (0.015, 0.0, 0.0)),
+           1: (3, 0.02, 0.99)}
+    nz, ny, nx = shape
+    g = lbm.Lattice(nx, ny, nz, tau=(0.9, 1.2), G=1.5, F_ext=(1e-5, 0, 0))
+    g.set_geometry(ns, gads)
+    for face, entry in res.items():
+        g.set_bc(face, entry[0], entry[1], entry[2],
+                 u=entry[3] if len(entry) > 3 else None)
+    p = oracle.Params(nx, ny, nz, tau=(float(np.float32(0.9)), float(np.float32(1.2))),
+                      G=1.5, Fext=(float(np.float32(1e-5)), 0, 0),
+                      reservoirs={k: (e[0], float(np.float32(e[1])), float(np.float32(e[2])))
+                                  + ((tuple(float(np.float32(v)) for v in e[3]),)
+                                     if len(e) > 3 else ())
+                                  for k, e in res.items()})
+    r = oracle.Sim(p, w64(ns), w64(gads))
+    f0 = synth.random_state(shape, 18).astype(np.float32)
+    g.set_populations(f0)
+    r.set_populations(f0.astype(np.float64))
+    for k in range(1, 4):
+        g.step(1)
+        r.step(1)
+        assert np.abs(g.populations() - r.f).max() <= 2e-6 * np.abs(r.f).max(), k
+    check_fields(g, r)
+    g.close()
+
+
+def test_couette_profile_matches_oracle_and_eq14():
+    """The Couette channel of Sec. 3.1 (H = 50, U0 = 0.01, n_s = 0.1,
+    boundary cells open): the GPU profile against the oracle after 6000
+    steps, and against Eq. 14 within the oracle's own margin."""
+    H, U0, ns, steps = 50, 0.01, 0.1, 6000
+    nx, shape = H + 1, (1, 4, H + 1)
+    ns_f = np.full(shape, ns)
+    ns_f[..., 0] = ns_f[..., H] = 0.0
+    g = lbm.Lattice(nx, 4, 1, tau=(1.0, 1.0), G=0.0)
+    g.set_geometry(ns_f)
+    g.set_bc(0, 1, 1.0, 0.01, u=(0.0, 0.0, 0.0))
+    g.set_bc(1, 1, 1.0, 0.01, u=(0.0, U0, 0.0))
+    g.init_equilibrium(np.full(shape, 1.0), np.full(shape, 0.01))
+    res = {0: (1, 1.0, float(np.float32(0.01)), (0.0, 0.0, 0.0)),
+           1: (1, 1.0, float(np.float32(0.01)), (0.0, float(np.float32(U0)), 0.0))}
+    r = oracle.Sim(oracle.Params(nx, 4, 1, tau=(1.0, 1.0), G=0.0, reservoirs=res),
+                   w64(ns_f))
+    r.init_equilibrium(np.full(shape, 1.0), w64(np.full(shape, 0.01)))
+    g.step(steps)
+    r.step(steps)
+    ug = g.fields()["u"][1, 0, 0, :].astype(np.float64)
+    ur = r.fields()["u"][1, 0, 0, :]
+    assert np.abs(ug - ur).max() <= 1e-5 * U0
+    r_ = math.sqrt(2 * ns / (1.0 / 6.0))
+    ua = U0 * np.sinh(r_ * np.arange(nx)) / math.sinh(r_ * H)
+    assert np.abs(ug - ua).max() <= 0.03 * U0
+    g.close()
