@@ -45,6 +45,10 @@ UNIT = "MLUPS"
 #                 write 2 x 19 x 4                          = 320
 BYTES_DENSITY = 160
 BYTES_COLLIDE = 320
+# 16-bit storages (2 B per population): offset kinds 84 / 168; local kinds
+# also read the node's own previous density (8 B) in both passes.
+STORAGE_BYTES = {"f32": (160, 320), "f16": (84, 168), "bf16": (84, 168),
+                 "f16l": (92, 176), "bf16l": (92, 176)}
 FALLBACK_HBM_GBS = 6800.0
 
 
@@ -271,21 +275,28 @@ def run_gpu(args, world, rank, local):
         import torch.distributed as dist
         dist.init_process_group("nccl")
 
-    n = args.size
-    case = synth.electrode((n, n, n))
-    nz, ny, nx = case.shape
+    if args.shape:
+        nx, ny, nz = (int(v) for v in args.shape.split(","))
+    else:
+        nx = ny = nz = args.size
+    case = synth.electrode((nz, ny, nx))
     N = case.n_nodes
+    storage = args.storage
+    bytes_density, bytes_collide = STORAGE_BYTES[storage]
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         lat = lbm.Lattice(nx, ny, nz, tau=case.tau, G=case.G, F_ext=case.F_ext,
-                          stream=stream)
+                          stream=stream, storage=storage, rho0=(0.5, 0.5))
     ctx = lat.ctx
     lat.set_geometry(case.ns, case.gads2)
     for face, (L, r1, r2) in case.reservoirs.items():
         lat.set_bc(face, L, r1, r2)
     lat.init_equilibrium(case.rho_a, case.rho_b)
     launch = None
-    if not args.no_autotune:
+    if args.launch_config:
+        launch = [int(v) for v in args.launch_config.split(",")]
+        lat.set_launch_config(*launch)
+    elif not args.no_autotune:
         import tempfile
         from paper_2206_11524_gb300 import autotune
         table = autotune.TuneTable(os.path.join(tempfile.mkdtemp(), "launch_table.json"))
@@ -350,8 +361,9 @@ def run_gpu(args, world, rank, local):
     d2h = 6 * 4 * N
 
     peak, peak_kind = _peaks()
-    achieved = BYTES_COLLIDE * N / (ms_collide / 1e3) / 1e9
-    traffic_bpn = _profiled_traffic("collide_stream")
+    dims = f"{nx}^3" if nx == ny == nz else f"{nx}x{ny}x{nz}"
+    achieved = bytes_collide * N / (ms_collide / 1e3) / 1e9
+    traffic_bpn = _profiled_traffic("collide_stream") if storage == "f32" else None
     if rank != 0:
         return 0
     serving = None
@@ -369,10 +381,11 @@ def run_gpu(args, world, rank, local):
         "steps": K, "warmup": args.warmup, "ms_per_step": ms_max / K,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"electrode imbibition {n}^3: synthetic "
+        "config": {"workload": f"electrode imbibition {dims}: synthetic "
                                "overlapping-sphere solid (n_s=1) + gray binder "
                                "blobs (n_s~U[0.2,0.9]), reservoirs at x=0 and "
-                               f"x={n - 1}, tau=1, G=1.75, f32 storage",
+                               f"x={nx - 1}, tau=1, G=1.75, {storage} storage",
+                   "storage": storage,
                    "nodes": N, "global_nodes": N * world,
                    "l2": "inputs larger than L2 (working set "
                          f"{lat.workspace.numel() / 1e9:.2f} GB)",
@@ -382,10 +395,10 @@ def run_gpu(args, world, rank, local):
                      "unit": "GB/s", "frac": achieved / peak,
                      "peak_kind": f"{peak_kind} hbm_gbs",
                      "kernel": "k_collide_stream",
-                     "algorithmic_bytes_per_node": BYTES_COLLIDE,
+                     "algorithmic_bytes_per_node": bytes_collide,
                      "traffic": (traffic_bpn * N if traffic_bpn else None)},
         "kernels_ms": {"density": ms_density, "collide_stream": ms_collide},
-        "step_hbm_gbs": (BYTES_DENSITY + BYTES_COLLIDE) * N / (ms_max / K / 1e3) / 1e9,
+        "step_hbm_gbs": (bytes_density + bytes_collide) * N / (ms_max / K / 1e3) / 1e9,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d / K,
                 "d2h_bytes_per_step": d2h / K},
         "gpu_launches": 2 * K,   # density pass + fused pass per step
@@ -408,9 +421,13 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--size", type=int, default=256)
+    ap.add_argument("--shape", default="", help="nx,ny,nz (overrides --size)")
+    ap.add_argument("--storage", default="f32", choices=sorted(STORAGE_BYTES))
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--launch-config", default="",
+                    help="density,even,odd launch shapes (skips the autotuner)")
     ap.add_argument("--serve-requests", type=int, default=24)
     ap.add_argument("--serve-lmax", type=int, default=160)
     ap.add_argument("--serve-steps-max", type=int, default=6000)

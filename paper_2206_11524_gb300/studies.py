@@ -1,0 +1,166 @@
+"""Validation studies on the GPU path at the paper's workload sizes.
+
+`laplace`     static droplets in homogeneous gray media (Sec. 3.3): the
+              pressure jump of Eq. A.6 against 1/R for several radii and
+              solid fractions; the slope of the fit is 2 gamma (3D Laplace
+              law), and gamma should not depend on n_s.
+`saturation`  imbibition into the synthetic electrode (Sec. 4): the
+              saturation curve S_1(t) of Eq. 19 for several population
+              storages, each against the float32 run of the same case.
+
+Run as ``python -m paper_2206_11524_gb300.studies <study> [options]``; the
+result is printed and written as JSON to ``--out``.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import time
+
+import numpy as np
+
+from . import lbm, synth
+
+# Flat-interface coexistence densities at G = 1.75 (both tau = 1), used as
+# the droplet's inner / outer densities so it starts near equilibrium.
+COEXIST_175 = (0.98739, 0.03548)
+
+
+def droplet_radius(rho_a):
+    """Equivalent radius of the fluid-1 droplet: its volume is the sum of the
+    fluid-1 density normalised between the extreme values, R = (3V/4pi)^1/3."""
+    lo, hi = float(rho_a.min()), float(rho_a.max())
+    vol = float(((rho_a.astype(np.float64) - lo) / (hi - lo)).sum())
+    return (3.0 * vol / (4.0 * math.pi)) ** (1.0 / 3.0)
+
+
+def pressure_jump(p, R, margin=10.0):
+    """Mean pressure inside r < R/2 minus the mean over the nodes farther than
+    R + margin from the centre of the (centred) droplet."""
+    n = p.shape[0]
+    c = n / 2 - 0.5
+    z, y, x = np.meshgrid(*(np.arange(n),) * 3, indexing="ij", sparse=True)
+    r = np.sqrt((x - c) ** 2 + (y - c) ** 2 + (z - c) ** 2)
+    inner = r < R / 2
+    outer = r > R + margin
+    return float(p[inner].mean() - p[outer].mean())
+
+
+def laplace(n=128, radii=(10, 15, 20, 25, 30), ns_values=(0.0, 0.3, 0.6),
+            steps=20000, G=1.75, storage="f32"):
+    rows = []
+    for ns in ns_values:
+        for R0 in radii:
+            case = synth.droplet(n=n, radius=float(R0), ns=ns, G=G,
+                                 hi=COEXIST_175[0], lo=COEXIST_175[1])
+            lat = lbm.Lattice(n, n, n, tau=(1.0, 1.0), G=G, storage=storage,
+                              rho0=(0.5, 0.5))
+            lat.set_geometry(case.ns)
+            lat.init_equilibrium(case.rho_a, case.rho_b)
+            lat.step(steps)
+            fl = lat.fields()
+            obs = lat.observables()
+            lat.close()
+            R = droplet_radius(fl["rho_a"])
+            dp = pressure_jump(fl["p"], R)
+            rows.append({"ns": ns, "R0": R0, "R": R, "dp": dp,
+                         "gamma_R": dp * R / 2.0,
+                         "max_u": float(np.abs(fl["u"]).max()),
+                         "mass": list(map(float, obs["mass"]))})
+    fits = {}
+    for ns in ns_values:
+        sel = [r for r in rows if r["ns"] == ns]
+        inv = np.array([1.0 / r["R"] for r in sel])
+        dp = np.array([r["dp"] for r in sel])
+        A = np.stack([inv, np.ones_like(inv)], axis=1)
+        (slope, icpt), *_ = np.linalg.lstsq(A, dp, rcond=None)
+        pred = A @ np.array([slope, icpt])
+        ss_res = float(((dp - pred) ** 2).sum())
+        ss_tot = float(((dp - dp.mean()) ** 2).sum())
+        fits[str(ns)] = {"gamma": slope / 2.0, "intercept": float(icpt),
+                         "r2": 1.0 - ss_res / ss_tot if ss_tot > 0 else 1.0,
+                         "gamma_largest_R": max(sel, key=lambda r: r["R"])["gamma_R"]}
+    g = [f["gamma"] for f in fits.values()]
+    return {"study": "laplace", "n": n, "steps": steps, "G": G, "storage": storage,
+            "rows": rows, "fits": fits,
+            "gamma_spread_rel": (max(g) - min(g)) / float(np.mean(g))}
+
+
+def _s1_curve(case, storage, steps, every):
+    import torch
+    nz, ny, nx = case.shape
+    lat = lbm.Lattice(nx, ny, nz, tau=case.tau, G=case.G, storage=storage,
+                      rho0=(0.5, 0.5))
+    lat.set_geometry(case.ns, case.gads2)
+    for face, (L, a, b) in case.reservoirs.items():
+        lat.set_bc(face, L, a, b)
+    lat.init_equilibrium(case.rho_a, case.rho_b)
+    curve, t_step = [], 0.0
+    for _ in range(steps // every):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        lat.step(every)
+        torch.cuda.synchronize()
+        t_step += time.perf_counter() - t0
+        curve.append(lat.observables()["sat1"])
+    lat.close()
+    return np.array(curve), case.n_nodes * steps / t_step / 1e6
+
+
+def saturation(shape=(256, 256, 256), storages=("f32", "f16", "bf16", "f16l", "bf16l"),
+               steps=50000, every=1000, seed=2206):
+    nx, ny, nz = shape
+    case = synth.electrode((nz, ny, nx), seed=seed)
+    out = {"study": "saturation", "shape": [nx, ny, nz], "steps": steps,
+           "every": every, "curves": {}, "linf_vs_f32": {}, "mlups": {}}
+    ref = None
+    for st in ("f32",) + tuple(s for s in storages if s != "f32"):
+        curve, mlups = _s1_curve(case, st, steps, every)
+        out["curves"][st] = curve.tolist()
+        out["mlups"][st] = mlups
+        if ref is None:
+            ref = curve
+        else:
+            out["linf_vs_f32"][st] = float(np.abs(curve - ref).max())
+    return out
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    sub = ap.add_subparsers(dest="study", required=True)
+    a = sub.add_parser("laplace")
+    a.add_argument("--n", type=int, default=128)
+    a.add_argument("--steps", type=int, default=20000)
+    a.add_argument("--radii", default="10,15,20,25,30")
+    a.add_argument("--ns", default="0,0.3,0.6")
+    a.add_argument("--out", default="")
+    b = sub.add_parser("saturation")
+    b.add_argument("--shape", default="256,256,256")
+    b.add_argument("--steps", type=int, default=50000)
+    b.add_argument("--every", type=int, default=1000)
+    b.add_argument("--storages", default="f32,f16,bf16,f16l,bf16l")
+    b.add_argument("--out", default="")
+    args = ap.parse_args(argv)
+    from . import build
+    build.build()
+    lbm.load()
+    if args.study == "laplace":
+        res = laplace(n=args.n, steps=args.steps,
+                      radii=tuple(int(v) for v in args.radii.split(",")),
+                      ns_values=tuple(float(v) for v in args.ns.split(",")))
+    else:
+        res = saturation(shape=tuple(int(v) for v in args.shape.split(",")),
+                         storages=tuple(args.storages.split(",")),
+                         steps=args.steps, every=args.every)
+    text = json.dumps(res, indent=1)
+    if args.out:
+        with open(args.out, "w") as fh:
+            fh.write(text)
+    summary = {k: v for k, v in res.items() if k not in ("rows", "curves")}
+    print(json.dumps(summary))
+    return 0
+
+
+if __name__ == "__main__":
+    raise SystemExit(main())

@@ -104,3 +104,15 @@ def test_tune_table_persists(tmp_path, monkeypatch):
     assert t.get(8, 8, 8, "f32") is None
     t.put(8, 8, 8, "f32", (1, 2, 3), {"density": [0.1]})
     assert autotune.TuneTable(str(tmp_path / "tab.json")).get(8, 8, 8, "f32") == (1, 2, 3)
+
+
+def test_droplet_measurement_helpers():
+    """Equivalent radius and pressure jump of the Laplace study on a
+    synthetic sharp sphere with a known inside / outside pressure."""
+    from paper_2206_11524_gb300 import studies, synth
+    n, R0 = 64, 12.0
+    case = synth.droplet(n=n, radius=R0, hi=0.98, lo=0.04)
+    R = studies.droplet_radius(case.rho_a)
+    assert abs(R - R0) < 0.02 * R0
+    p = np.where(case.rho_a > 0.5, 0.31, 0.30)
+    assert abs(studies.pressure_jump(p, R) - 0.01) < 1e-12
