@@ -234,33 +234,9 @@ def serving_leg(args):
     graphs) against one-at-a-time float32 runs on the same seeded trace of
     heterogeneous requests, offered at 0.9 of the sequential capacity."""
     from paper_2206_11524_gb300 import serve
-    reqs = serve.make_requests(n_req=args.serve_requests, seed=2206, L_min=32,
-                               L_max=args.serve_lmax, steps_min=1000,
-                               steps_max=args.serve_steps_max, base_n=args.serve_lmax)
-    work = [r.nodes * r.steps for r in reqs]
-    # calibrate the sequential capacity on a few requests of the trace
-    probe = sorted(reqs, key=lambda r: r.nodes)[len(reqs) // 2 - 1: len(reqs) // 2 + 2]
-    for r in probe:
-        r.arrival = 0.0
-    cal = serve.summarize(serve.run_sequential(probe))
-    rate = 0.9 * cal["mlups"] * 1e6 / (sum(work) / len(work))
-    import numpy as np
-    rng = np.random.default_rng(2207)
-    t = 0.0
-    for r in reqs:
-        t += float(rng.exponential(1.0 / rate))
-        r.arrival = t
-    seq = serve.summarize(serve.run_sequential(reqs))
-    srv = serve.Server(storage=args.serve_storage, tick_steps=400)
-    bat = serve.summarize(srv.run(reqs))
-    bat.update(storage=args.serve_storage, graph_launches=srv.graph_launches,
-               captures=srv.captures, ticks=srv.ticks)
-    seq.update(storage="f32")
-    return {"trace": f"{len(reqs)} requests, cubic L in [32, {args.serve_lmax}] "
-                     f"log-uniform, steps U{{1000..{args.serve_steps_max}}}, Poisson "
-                     f"arrivals at 0.9 x sequential capacity ({rate:.2f}/s), seeded "
-                     "electrode crops with per-request G and binder wettability",
-            "batched": bat, "sequential": seq}
+    return serve.compare(n_req=args.serve_requests, L_min=32, L_max=args.serve_lmax,
+                         steps_min=1000, steps_max=args.serve_steps_max,
+                         storage=args.serve_storage, load=0.9, seed=2206)
 
 
 def run_gpu(args, world, rank, local):

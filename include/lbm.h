@@ -168,8 +168,20 @@ LBM_API lbm_status lbm_set_bc_velocity(lbm_ctx *ctx, int face, int layers,
 
 /* Advance n_steps time steps (Eq. 1 plus the reservoirs), asynchronously on
  * the context's stream.  Each step launches the density pass and the fused
- * force/collide/bounce-back/stream pass.  n_steps = 0 is a no-op. */
+ * force/collide/bounce-back/stream pass, or the single-pass sweep when
+ * lbm_set_single_pass enabled it.  n_steps = 0 is a no-op. */
 LBM_API lbm_status lbm_step(lbm_ctx *ctx, int n_steps);
+
+/* Single-pass stepping for lbm_step (planes > 0; 0 = two passes, the
+ * default): each step reads every population once.  The lattice is cut into
+ * boxes of full x-rows, 8 rows by `planes` planes; one launch marches every
+ * box along z, computing the densities of the next plane into shared memory
+ * and colliding the current plane's inner rows with them; the last row and
+ * plane of each box (its seams, whose populations no other box may see
+ * updated) are then updated by a second launch.  Results are bit-identical
+ * to the two-pass step.  Needs nx <= 256 (EINVAL otherwise).  lbm_density /
+ * lbm_collide_stream and the batched entry points keep the two passes. */
+LBM_API lbm_status lbm_set_single_pass(lbm_ctx *ctx, int planes);
 
 /* The two halves of one step, for callers that time or interleave them:
  * lbm_density (rho_sigma of Eq. A.4 at every node) followed by

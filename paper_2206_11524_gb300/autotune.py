@@ -1,5 +1,6 @@
 """Autotuner of the launch shapes (thread-block shape and register budget) of
-the density pass and of the fused pass on even and odd steps.
+the density pass and of the fused pass on even and odd steps, and
+optionally of the choice between the two-pass and the single-pass step.
 
 `tune(nx, ny, nz, storage)` times every shape on a scratch lattice of that
 size and storage (a synthetic gray medium with two-phase densities; the
@@ -79,8 +80,36 @@ def _time(lat, fn, reps):
     return a.elapsed_time(b) / reps
 
 
-def tune(nx, ny, nz, storage="f32", reps=10):
-    """Fastest (density, even, odd) launch shapes and all timings (ms)."""
+def _step_ms(lat, steps=10):
+    import torch
+    st = lat.stream
+    lat.step(2)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(st)
+    lat.step(steps)
+    b.record(st)
+    b.synchronize()
+    return a.elapsed_time(b) / steps
+
+
+def _single_pass_candidates(ny, nz, sms):
+    """Box depths whose boxes fill one or two waves of two boxes per SM."""
+    nyb = (ny + 7) // 8
+    out = []
+    for waves in (1, 2):
+        nzc = max(1, min(nz, (waves * 2 * sms) // nyb))
+        planes = max(1, round(nz / nzc))
+        if planes not in out:
+            out.append(planes)
+    return out
+
+
+def tune(nx, ny, nz, storage="f32", reps=10, single_pass=False, margin=0.03):
+    """Fastest (density, even, odd) launch shapes and all timings (ms).  With
+    single_pass, whole steps of the best two-pass shapes are timed against
+    the single-pass step at box depths that fit the SM count; a single-pass
+    depth is kept (fourth entry, 0 = two passes) only if it is faster by
+    more than `margin`."""
     lat = _scratch(nx, ny, nz, storage)
     ctx = lat.ctx
     timings = {"density": [], "even": [], "odd": []}
@@ -115,20 +144,39 @@ def tune(nx, ny, nz, storage="f32", reps=10):
         lbm.lbm_set_launch_config(ctx, best_d, best_e, o)
         timings["odd"].append(fused_only(1))
     best_o = int(np.argmin(timings["odd"]))
+    cfg = (best_d, best_e, best_o)
+    if single_pass and nx <= lbm.SINGLE_PASS_MAX_NX:
+        import torch
+        lbm.lbm_set_launch_config(ctx, *cfg)
+        two = _step_ms(lat)
+        timings["two_pass_step"] = two
+        best_sp, best_ms = 0, two * (1.0 - margin)
+        sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+        for planes in _single_pass_candidates(ny, nz, sms):
+            lat.set_single_pass(planes)
+            ms = _step_ms(lat)
+            timings[f"single_pass_{planes}"] = ms
+            if ms < best_ms:
+                best_sp, best_ms = planes, ms
+        lat.set_single_pass(0)
+        cfg = cfg + (best_sp,)
     lat.close()
-    return (best_d, best_e, best_o), timings
+    return cfg, timings
 
 
-def apply(lattice, table: TuneTable | None = None, tune_if_missing=True):
+def apply(lattice, table: TuneTable | None = None, tune_if_missing=True,
+          single_pass=False):
     """Configure `lattice` from the table, tuning (and recording) its size
-    and storage first when the table has no entry."""
+    and storage first when the table has no entry.  An entry's optional
+    fourth value is the single-pass box depth (0: two passes)."""
     table = table or TuneTable()
     nz, ny, nx = lattice.shape
     storage = lattice.storage_name
     cfg = table.get(nx, ny, nz, storage)
     if cfg is None and tune_if_missing:
-        cfg, timings = tune(nx, ny, nz, storage)
+        cfg, timings = tune(nx, ny, nz, storage, single_pass=single_pass)
         table.put(nx, ny, nz, storage, cfg, timings)
     if cfg is not None:
-        lbm.lbm_set_launch_config(lattice.ctx, *cfg)
+        lbm.lbm_set_launch_config(lattice.ctx, *cfg[:3])
+        lattice.set_single_pass(cfg[3] if len(cfg) > 3 else 0)
     return cfg

@@ -37,6 +37,7 @@ struct lbm_ctx {
   bool have_state;
   uint64_t bc_version;    // bumped by every lbm_set_bc
   int launch_cfg[3];      // launch shapes: density, even fused, odd fused
+  int single_pass_zc;     // > 0: lbm_step sweeps once, boxes of this many planes
   std::string err;
 };
 
@@ -190,6 +191,18 @@ lbm_status upload(lbm_ctx *c, float *dst, const float *src, size_t n) {
   return LBM_OK;
 }
 
+// Host bookkeeping after the fused pass of a step.
+void finish_step(lbm_ctx *c) {
+  // The reservoirs in force now reset their layers at the end of this step.
+  c->sp.res = c->res_current;
+  // *_LOCAL: the densities of this step are the encoding densities now.
+  if (hmcsc::storage_local(c->sp.storage)) {
+    c->enc = 1 - c->enc;
+    set_density_views(c);
+  }
+  c->t += 1;
+}
+
 }  // namespace
 
 extern "C" {
@@ -254,6 +267,7 @@ lbm_status lbm_create(const lbm_params *params, void *d_workspace,
   c->have_state = false;
   c->bc_version = 0;
   c->launch_cfg[0] = c->launch_cfg[1] = c->launch_cfg[2] = 0;
+  c->single_pass_zc = 0;
   // Zero the whole workspace once so padding lanes hold defined values.
   cudaError_t e = cudaMemsetAsync(d_workspace, 0, need, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
@@ -502,14 +516,7 @@ lbm_status lbm_collide_stream(lbm_ctx *c) {
   cudaError_t e = hmcsc::launch_collide_stream(c->sp, c->ws, parity(c),
                                                 c->launch_cfg[1 + parity(c)], c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "collide/stream kernel");
-  // The reservoirs in force now reset their layers at the end of this step.
-  c->sp.res = c->res_current;
-  // *_LOCAL: the densities of this step are the encoding densities now.
-  if (hmcsc::storage_local(c->sp.storage)) {
-    c->enc = 1 - c->enc;
-    set_density_views(c);
-  }
-  c->t += 1;
+  finish_step(c);
   return LBM_OK;
 }
 
@@ -520,11 +527,31 @@ lbm_status lbm_step(lbm_ctx *c, int n_steps) {
   if (!c->have_geometry || !c->have_state)
     return fail(c, LBM_ESTATE, "set geometry and state before stepping");
   for (int k = 0; k < n_steps; ++k) {
+    if (c->single_pass_zc > 0) {
+      // runs of about single_pass_zc planes along z
+      const int nz = c->params.nz;
+      int nzc = (nz + c->single_pass_zc / 2) / c->single_pass_zc;
+      nzc = nzc < 1 ? 1 : (nzc > nz ? nz : nzc);
+      cudaError_t e = hmcsc::launch_single_pass(c->sp, c->ws, parity(c), nzc, c->stream);
+      if (e != cudaSuccess) return cuda_fail(c, e, "single-pass kernels");
+      c->rho_at = c->t;
+      finish_step(c);
+      continue;
+    }
     lbm_status st = lbm_density(c);
     if (st) return st;
     st = lbm_collide_stream(c);
     if (st) return st;
   }
+  return LBM_OK;
+}
+
+lbm_status lbm_set_single_pass(lbm_ctx *c, int planes) {
+  if (!c) return LBM_EINVAL;
+  if (planes < 0) return fail(c, LBM_EINVAL, "planes must be >= 0");
+  if (planes > 0 && c->params.nx > hmcsc::kSinglePassMaxNx)
+    return fail(c, LBM_EINVAL, "the single-pass step needs nx <= %d", hmcsc::kSinglePassMaxNx);
+  c->single_pass_zc = planes;
   return LBM_OK;
 }
 

@@ -136,6 +136,29 @@ __device__ __forceinline__ void first_moment(const float (&v)[kQ],
   }
 }
 
+// A read-only load the compiler may neither merge with an earlier load of
+// the same address nor hoist: keeps a value that is needed late from
+// occupying a register from the start of the kernel.
+__device__ __forceinline__ float2 ld_late(const float2 *ptr) {
+  float2 v;
+  asm volatile("ld.global.nc.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(ptr));
+  return v;
+}
+
+// Where a pass finds the densities of the current step at x + (dx, dy, dz):
+// `at` for the force stencil, `late` for the encoding reference of the
+// *_LOCAL storages (a load the compiler keeps next to its use).
+struct GlobalRho {  // the density array written by the density pass
+  const float2 *__restrict__ rho;
+  const Geo &g;
+  __device__ __forceinline__ float2 at(int dx, int dy, int dz) const {
+    return __ldg(&rho[g.node(dx, dy, dz)]);
+  }
+  __device__ __forceinline__ float2 late(int dx, int dy, int dz) const {
+    return ld_late(&rho[g.node(dx, dy, dz)]);
+  }
+};
+
 // Total force per unit mass of each component, F_tot,sigma / rho_sigma
 // (Eqs. 3-5; rho_sigma cancels against the prefactor of Eqs. 3-4 and the
 // density ratio of Eq. 5, so no division by a vanishing component density):
@@ -145,9 +168,8 @@ __device__ __forceinline__ void first_moment(const float (&v)[kQ],
 // Table 1; the indicator of Eq. 4 is the component's own fraction).  With
 // one fraction for both (PC = false) A_1 = A_2.  Opposite directions are
 // summed as pairs, so a uniform field gives exactly zero.
-template <bool PC>
-__device__ __forceinline__ void force_per_mass(const StepParams &p,
-                                               const float2 *__restrict__ rho,
+template <bool PC, typename RS>
+__device__ __forceinline__ void force_per_mass(const StepParams &p, const RS &rs,
                                                const float *__restrict__ ads,
                                                const float *__restrict__ ads2,
                                                const Geo &g, float rho_tot,
@@ -158,8 +180,8 @@ __device__ __forceinline__ void force_per_mass(const StepParams &p,
   for (int i = 1; i <= 9; ++i) {
     const int mp = g.node(cx(i), cy(i), cz(i));
     const int mm = g.node(-cx(i), -cy(i), -cz(i));
-    const float2 rp = __ldg(&rho[mp]);
-    const float2 rm = __ldg(&rho[mm]);
+    const float2 rp = rs.at(cx(i), cy(i), cz(i));
+    const float2 rm = rs.at(-cx(i), -cy(i), -cz(i));
     const float ap = __ldg(&ads[mp]);
     const float am = __ldg(&ads[mm]);
     const float d1 = wgt(i) * (rp.x - rm.x);
@@ -249,35 +271,25 @@ __device__ __forceinline__ void reservoir_state(const StepParams &p, bool maybe,
   }
 }
 
-// Store the post-collision population i of component s; it becomes
-// population i of node x + c_i at t + 1.
-// A read-only load the compiler may neither merge with an earlier load of
-// the same address nor hoist: keeps a value that is needed late from
-// occupying a register from the start of the kernel.
-__device__ __forceinline__ float2 ld_late(const float2 *ptr) {
-  float2 v;
-  asm volatile("ld.global.nc.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(ptr));
-  return v;
-}
-
 // Store the post-collision pair (both components) of direction i; it
 // becomes the pair of direction i of node x + c_i at t + 1.  Encoding
 // reference: w_i times the destination's density at this step (*_LOCAL;
 // rho_s for the rest population, the density pass's value otherwise), or the
 // constants w_i rho0_sigma (*_OFFSET).
-template <int PARITY, int ST>
+template <int PARITY, int ST, typename RS>
 __device__ __forceinline__ void put2(const StepParams &p, const Workspace &w,
-                                     const Geo &g, int i, float o1, float o2,
-                                     float r1, float r2) {
+                                     const Geo &g, const RS &rs, int i, float o1,
+                                     float o2, float r1, float r2) {
   using C = Codec2<ST>;
   typename C::T2 *f = static_cast<typename C::T2 *>(w.f);
-  float2 ref = make_float2(p.ref[0][wclass(i)], p.ref[1][wclass(i)]);
+  // encoding reference times the codec's scale (exact)
+  float2 ref = make_float2(p.ref[0][wclass(i)] * C::kScale, p.ref[1][wclass(i)] * C::kScale);
   if (storage_local(ST)) {
-    const float2 rd = i == 0 ? make_float2(r1, r2)
-                             : ld_late(&w.rho[g.node(cx(i), cy(i), cz(i))]);
-    ref = make_float2(__fmul_rn(wgt(i), rd.x), __fmul_rn(wgt(i), rd.y));
+    const float2 rd = i == 0 ? make_float2(r1, r2) : rs.late(cx(i), cy(i), cz(i));
+    const float ws = wgt(i) * C::kScale;
+    ref = make_float2(__fmul_rn(ws, rd.x), __fmul_rn(ws, rd.y));
   }
-  const typename C::T2 e = C::enc(o1, o2, ref);
+  const typename C::T2 e = C::enc_s(o1, o2, ref);
   if (PARITY == 0)
     pop_base(f, g, 0, 0, 0)[opp(i) * kTile] = e;
   else
@@ -323,9 +335,10 @@ struct Relax {
   }
 };
 
-template <int PARITY, int ST>
+template <int PARITY, int ST, typename RS>
 __device__ __forceinline__ void collide_put2(const StepParams &p, const Workspace &w,
-                                             const Geo &g, const float (&v1)[kQ],
+                                             const Geo &g, const RS &rs,
+                                             const float (&v1)[kQ],
                                              const float (&v2)[kQ], float r1,
                                              float r2, const float (&u1)[3],
                                              const float (&u2)[3], float ns1,
@@ -336,17 +349,18 @@ __device__ __forceinline__ void collide_put2(const StepParams &p, const Workspac
     float o1i, o1j, o2i, o2j;
     c1.pair(i, u1, v1, o1i, o1j);
     c2.pair(i, u2, v2, o2i, o2j);
-    put2<PARITY, ST>(p, w, g, i, o1i, o2i, r1, r2);
-    put2<PARITY, ST>(p, w, g, i + 9, o1j, o2j, r1, r2);
+    put2<PARITY, ST>(p, w, g, rs, i, o1i, o2i, r1, r2);
+    put2<PARITY, ST>(p, w, g, rs, i + 9, o1j, o2j, r1, r2);
   }
-  put2<PARITY, ST>(p, w, g, 0, c1.rest(v1), c2.rest(v2), r1, r2);
+  put2<PARITY, ST>(p, w, g, rs, 0, c1.rest(v1), c2.rest(v2), r1, r2);
 }
 
-template <int PARITY, int ST, bool PC>
-__device__ __forceinline__ void collide_body(const StepParams &p,
-                                             const Workspace &w, bool maybe_res,
-                                             int x, int y, int z) {
-  const Geo g = make_geo(p, x, y, z);
+// Moments, forces, equilibrium velocity and collision of node (x, y, z)
+// given its neighbourhood g and the source of the step's densities.
+template <int PARITY, int ST, bool PC, typename RS>
+__device__ __forceinline__ void collide_node(const StepParams &p, const Workspace &w,
+                                             const Geo &g, const RS &rs,
+                                             bool maybe_res, int x, int y, int z) {
   float f1[kQ], f2[kQ];
   load_pops<PARITY, ST>(p, w, g, f1, f2);
   reservoir_state(p, maybe_res, x, y, z, f1, f2);
@@ -356,7 +370,7 @@ __device__ __forceinline__ void collide_body(const StepParams &p,
   first_moment(f2, j2);
 
   float g1[3], g2[3];
-  force_per_mass<PC>(p, w.rho, w.ads, w.ads2, g, r1 + r2, g1, g2);
+  force_per_mass<PC>(p, rs, w.ads, w.ads2, g, r1 + r2, g1, g2);
 
   // Eq. 6: common velocity sum_s j_s/tau_s / sum_s rho_s/tau_s, then the
   // Shan-Chen shift tau_s F_tot,s / rho_s = tau_s g_s.
@@ -371,7 +385,15 @@ __device__ __forceinline__ void collide_body(const StepParams &p,
 
   const float ns1 = w.ns[g.node(0, 0, 0)];
   const float ns2 = PC ? w.ns2[g.node(0, 0, 0)] : ns1;
-  collide_put2<PARITY, ST>(p, w, g, f1, f2, r1, r2, u1, u2, ns1, ns2);
+  collide_put2<PARITY, ST>(p, w, g, rs, f1, f2, r1, r2, u1, u2, ns1, ns2);
+}
+
+template <int PARITY, int ST, bool PC>
+__device__ __forceinline__ void collide_body(const StepParams &p,
+                                             const Workspace &w, bool maybe_res,
+                                             int x, int y, int z) {
+  const Geo g = make_geo(p, x, y, z);
+  collide_node<PARITY, ST, PC>(p, w, g, GlobalRho{w.rho, g}, maybe_res, x, y, z);
 }
 
 
@@ -472,7 +494,7 @@ __global__ void __launch_bounds__(kTile * kFieldsBY * kFieldsBZ)
   first_moment(f2, j2);
   float g1[3], g2[3];
   const float rho = r1 + r2;
-  force_per_mass<PC>(p, w.rho, w.ads, w.ads2, g, rho, g1, g2);
+  force_per_mass<PC>(p, GlobalRho{w.rho, g}, w.ads, w.ads2, g, rho, g1, g2);
   const float fluid = 1.0f - w.ns[g.node(0, 0, 0)];
   const float fluid2 = PC ? 1.0f - w.ns2[g.node(0, 0, 0)] : fluid;
   const long long L = p.nlin;
@@ -522,6 +544,146 @@ __global__ void k_init_equilibrium(StepParams p, Workspace w,
       b[i * kTile] = C::enc(__fmul_rn(wgt(i), r1), __fmul_rn(wgt(i), r2), ref);
     }
   }
+}
+
+// ---- single-pass step: density and fused pass in one sweep ----
+//
+// The two-pass step reads every population twice (160 B/node for the
+// density pass).  A single sweep must know the densities of a node's
+// neighbours before it collides the node, and a block cannot recompute a
+// neighbour's density from that neighbour's populations if another block may
+// already have updated them in place.  So the lattice is cut into boxes of
+// full x-rows: rows [y0, y0 + kSpBY) and nzc runs of planes along z (run c
+// covers [c nz / nzc, (c + 1) nz / nzc), so runs differ by one plane at
+// most and the grid is nyb x nzc boxes, a number the host can fit to the
+// SM count).  The last row
+// and the last plane of every box are seams.  One launch (k_sp_bulk) marches
+// each box along z; per plane it computes the densities of the next plane --
+// its own rows plus the seam row of the box below -- into a shared-memory
+// ring of four planes, and collides the plane's bulk rows with the force
+// stencil read from the ring.  Every density a box needs belongs to one of
+// its own nodes (computed before that node is updated) or to a seam of
+// another box (not updated by this launch).  Each box writes the densities of
+// its own nodes to the density array; a second launch (k_sp_seams) then
+// updates the seam rows and planes with the two-pass code, reading the
+// completed array.  In-place AA streaming keeps every write of a node inside
+// that node's own (slot, node) set, so no update disturbs another node's
+// reads.  Results are bit-identical to the two-pass step (same densities,
+// same arithmetic).
+constexpr int kSpBY = 8;            // rows per box, the last one a seam
+constexpr int kSpMaxThreads = 256;  // one thread per x: nx <= 256
+constexpr int kSpRingPlanes = 4;
+
+// First plane of run c of nzc runs along nz planes.
+__host__ __device__ __forceinline__ int sp_run_start(int c, int nz, int nzc) {
+  return (int)(((long long)c * nz) / nzc);
+}
+
+__host__ __device__ constexpr size_t sp_ring_bytes(int ncol) {
+  return sizeof(float2) * kSpRingPlanes * (kSpBY + 1) * (size_t)ncol;
+}
+
+// Densities of x +- 1, y +- 1, z +- 1 from the ring.
+struct RingRho {
+  const float2 *row[3];  // ring row of the node's y in planes z - 1, z, z + 1
+  int stride;            // one ring row (columns)
+  int xm, xc, xp;        // columns of x - 1, x, x + 1 (periodic)
+  __device__ __forceinline__ float2 at(int dx, int dy, int dz) const {
+    return row[dz + 1][dy * stride + (dx < 0 ? xm : (dx > 0 ? xp : xc))];
+  }
+  __device__ __forceinline__ float2 late(int dx, int dy, int dz) const {
+    return at(dx, dy, dz);
+  }
+};
+
+// Density pair of node (x, y, z) at the current step.
+template <int PARITY, int ST>
+__device__ __forceinline__ float2 node_density(const StepParams &p, const Workspace &w,
+                                               const Geo &g, int x, int y, int z) {
+  float v1[kQ], v2[kQ];
+  load_pops<PARITY, ST>(p, w, g, v1, v2);
+  reservoir_state(p, p.res.any != 0, x, y, z, v1, v2);
+  return make_float2(sum19(v1), sum19(v2));
+}
+
+template <int PARITY, int ST, bool PC>
+__global__ void __launch_bounds__(kSpMaxThreads, 2)
+    k_sp_bulk(StepParams p, Workspace w, int nzc) {
+  extern __shared__ float2 ring[];  // [kSpRingPlanes][kSpBY + 1][ncol]
+  const int ncol = blockDim.x;
+  const int x = threadIdx.x;
+  const bool active = x < p.nx;
+  const int y0 = blockIdx.x * kSpBY, yend = min(y0 + kSpBY, p.ny);
+  const int nr = yend - y0;  // own rows; ring row r <-> y0 - 1 + r
+  const int z0 = sp_run_start(blockIdx.y, p.nz, nzc);
+  const int zend = sp_run_start(blockIdx.y + 1, p.nz, nzc);
+  const int plane_stride = (kSpBY + 1) * ncol;
+
+  // densities of relative plane k (z = z0 - 1 + k) into ring slot k % 4;
+  // own nodes (rows 1..nr, planes z0..zend-1) also go to the density array
+  auto rho_plane = [&](int k) {
+    int z = z0 - 1 + k;
+    const bool own_plane = k >= 1;
+    if (z < 0) z += p.nz;
+    float2 *dst = ring + (k & 3) * plane_stride;
+    if (!active) return;
+#pragma unroll 2
+    for (int r = 0; r <= nr; ++r) {
+      int y = y0 - 1 + r;
+      if (y < 0) y += p.ny;
+      const Geo g = make_geo(p, x, y, z);
+      const float2 rho = node_density<PARITY, ST>(p, w, g, x, y, z);
+      dst[r * ncol + x] = rho;
+      if (own_plane && r >= 1) w.rho[g.node(0, 0, 0)] = rho;
+    }
+  };
+
+  rho_plane(0);
+  rho_plane(1);
+  const int xm = x == 0 ? p.nx - 1 : x - 1;
+  const int xp = x == p.nx - 1 ? 0 : x + 1;
+  for (int j = 0; j + 1 < zend - z0; ++j) {
+    rho_plane(j + 2);
+    __syncthreads();
+    if (!active) continue;
+    const int z = z0 + j;
+    for (int r = 1; r < nr; ++r) {
+      const int y = y0 - 1 + r;
+      const Geo g = make_geo(p, x, y, z);
+      RingRho rr;
+      rr.row[0] = ring + (j & 3) * plane_stride + r * ncol;
+      rr.row[1] = ring + ((j + 1) & 3) * plane_stride + r * ncol;
+      rr.row[2] = ring + ((j + 2) & 3) * plane_stride + r * ncol;
+      rr.stride = ncol;
+      rr.xm = xm;
+      rr.xc = x;
+      rr.xp = xp;
+      collide_node<PARITY, ST, PC>(p, w, g, rr, p.res.any != 0, x, y, z);
+    }
+  }
+}
+
+// Seam rows of every box (all planes), then seam planes of every box (the
+// rows that are not seam rows): the two-pass fused update with the density
+// array the bulk launch completed.  Blocks of 32 x 4 threads.
+template <int PARITY, int ST, bool PC>
+__global__ void __launch_bounds__(kTile * 4, 4)
+    k_sp_seams(StepParams p, Workspace w, int nzc, int part) {
+  const int x = blockIdx.x * kTile + threadIdx.x;
+  int y, z;
+  if (part == 0) {
+    y = min(blockIdx.y * kSpBY + kSpBY - 1, p.ny - 1);
+    z = blockIdx.z * 4 + threadIdx.y;
+    if (z >= p.nz) return;
+  } else {
+    y = blockIdx.y * 4 + threadIdx.y;
+    z = sp_run_start(blockIdx.z + 1, p.nz, nzc) - 1;
+    if (y >= p.ny) return;
+    const int yseam = min((y / kSpBY) * kSpBY + kSpBY - 1, p.ny - 1);
+    if (y == yseam) return;
+  }
+  if (x >= p.nx) return;
+  collide_body<PARITY, ST, PC>(p, w, p.res.any != 0, x, y, z);
 }
 
 // ---- batched kernels: several lattices per launch ----

@@ -49,33 +49,49 @@ __host__ __device__ constexpr int wclass(int i) {
 // Half offsets are kept scaled by 2^14 (see above).
 constexpr float kHalfScale = 16384.0f, kHalfUnscale = 1.0f / 16384.0f;
 
-// The stored pair (sigma = 1, 2) of one direction at one node.
+// The stored pair (sigma = 1, 2) of one direction at one node.  enc_s
+// takes the reference already multiplied by kScale (exact: a power of two),
+// so the half encode is one fused multiply-add per value: f * 2^14 - r 2^14
+// rounds to the same float as (f - r) * 2^14 because scaling by a power of
+// two commutes with rounding.
 template <int ST> struct Codec2;
 template <> struct Codec2<kF32> {
   using T2 = float2;
+  static constexpr float kScale = 1.0f;
   static __device__ __forceinline__ float2 dec(T2 v, float2) { return v; }
+  static __device__ __forceinline__ T2 enc_s(float f1, float f2, float2) {
+    return make_float2(f1, f2);
+  }
   static __device__ __forceinline__ T2 enc(float f1, float f2, float2) {
     return make_float2(f1, f2);
   }
 };
 template <> struct Codec2<kF16> {
   using T2 = __half2;
+  static constexpr float kScale = kHalfScale;
   static __device__ __forceinline__ float2 dec(T2 v, float2 r) {
     const float2 h = __half22float2(v);
     return make_float2(fmaf(h.x, kHalfUnscale, r.x), fmaf(h.y, kHalfUnscale, r.y));
   }
+  static __device__ __forceinline__ T2 enc_s(float f1, float f2, float2 rs) {
+    return __floats2half2_rn(fmaf(f1, kHalfScale, -rs.x), fmaf(f2, kHalfScale, -rs.y));
+  }
   static __device__ __forceinline__ T2 enc(float f1, float f2, float2 r) {
-    return __floats2half2_rn((f1 - r.x) * kHalfScale, (f2 - r.y) * kHalfScale);
+    return enc_s(f1, f2, make_float2(r.x * kHalfScale, r.y * kHalfScale));
   }
 };
 template <> struct Codec2<kBF16> {
   using T2 = __nv_bfloat162;
+  static constexpr float kScale = 1.0f;
   static __device__ __forceinline__ float2 dec(T2 v, float2 r) {
     const float2 h = __bfloat1622float2(v);
     return make_float2(r.x + h.x, r.y + h.y);
   }
-  static __device__ __forceinline__ T2 enc(float f1, float f2, float2 r) {
+  static __device__ __forceinline__ T2 enc_s(float f1, float f2, float2 r) {
     return __floats2bfloat162_rn(f1 - r.x, f2 - r.y);
+  }
+  static __device__ __forceinline__ T2 enc(float f1, float f2, float2 r) {
+    return enc_s(f1, f2, r);
   }
 };
 template <> struct Codec2<kF16L> : Codec2<kF16> {};
@@ -234,6 +250,8 @@ cudaError_t launch_batch_collide(const BatchArgs &a, int storage, cudaStream_t s
                                   cudaStream_t);                               \
   cudaError_t launch_init_##SUF(const StepParams &, const Workspace &,         \
                                 const float *, const float *, cudaStream_t);   \
+  cudaError_t launch_single_pass_##SUF(const StepParams &, const Workspace &,  \
+                                       int, int, cudaStream_t);                \
   cudaError_t launch_batch_density_##SUF(const BatchArgs &, cudaStream_t);     \
   cudaError_t launch_batch_collide_##SUF(const BatchArgs &, cudaStream_t);
 HMCSC_DECLARE_STORAGE_LAUNCHERS(f32)
@@ -260,6 +278,13 @@ cudaError_t launch_collide_stream(const StepParams &p, const Workspace &w,
                                   int parity, int cfg, cudaStream_t s);
 cudaError_t launch_fields(const StepParams &p, const Workspace &w, int parity,
                           cudaStream_t s);
+// One whole step in a single sweep over the populations (bulk boxes of
+// kSpBY rows x nz / nzc planes, then their seams); needs nx <= kSinglePassMaxNx
+// and 1 <= nzc <= nz.
+// Leaves the step's densities in w.rho like launch_density.
+constexpr int kSinglePassMaxNx = 256;
+cudaError_t launch_single_pass(const StepParams &p, const Workspace &w, int parity,
+                               int nzc, cudaStream_t s);
 cudaError_t launch_reduce(const StepParams &p, const Workspace &w,
                           cudaStream_t s);
 

@@ -196,6 +196,17 @@ cudaError_t launch_fields(const StepParams &p, const Workspace &w, int parity,
   }
 }
 
+cudaError_t launch_single_pass(const StepParams &p, const Workspace &w, int parity,
+                               int nzc, cudaStream_t s) {
+  switch (p.storage) {
+    case kF16: return launch_single_pass_f16(p, w, parity, nzc, s);
+    case kBF16: return launch_single_pass_bf16(p, w, parity, nzc, s);
+    case kF16L: return launch_single_pass_f16l(p, w, parity, nzc, s);
+    case kBF16L: return launch_single_pass_bf16l(p, w, parity, nzc, s);
+    default: return launch_single_pass_f32(p, w, parity, nzc, s);
+  }
+}
+
 cudaError_t launch_batch_density(const BatchArgs &a, int storage, cudaStream_t s) {
   if (a.n <= 0 || a.prefix[a.n] <= 0) return cudaSuccess;
   switch (storage) {

@@ -82,6 +82,34 @@ cudaError_t HMCSC_NAME(launch_init)(const StepParams &p, const Workspace &w,
   return cudaGetLastError();
 }
 
+namespace {
+template <int PARITY, bool PC>
+cudaError_t single_pass(const StepParams &p, const Workspace &w, int nzc, cudaStream_t s) {
+  const int ncol = p.ntx * kTile;
+  const size_t smem = sp_ring_bytes(ncol);
+  static bool attr_set = false;  // the largest ring any lattice may need
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_sp_bulk<PARITY, kST, PC>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sp_ring_bytes(kSpMaxThreads));
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  const int nyb = (p.ny + kSpBY - 1) / kSpBY;
+  k_sp_bulk<PARITY, kST, PC><<<dim3(nyb, nzc), ncol, smem, s>>>(p, w, nzc);
+  k_sp_seams<PARITY, kST, PC><<<dim3(p.ntx, nyb, (p.nz + 3) / 4), dim3(kTile, 4), 0, s>>>(p, w, nzc, 0);
+  k_sp_seams<PARITY, kST, PC><<<dim3(p.ntx, (p.ny + 3) / 4, nzc), dim3(kTile, 4), 0, s>>>(p, w, nzc, 1);
+  return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t HMCSC_NAME(launch_single_pass)(const StepParams &p, const Workspace &w,
+                                           int parity, int nzc, cudaStream_t s) {
+  if (w.ns2)
+    return parity == 0 ? single_pass<0, true>(p, w, nzc, s) : single_pass<1, true>(p, w, nzc, s);
+  return parity == 0 ? single_pass<0, false>(p, w, nzc, s) : single_pass<1, false>(p, w, nzc, s);
+}
+
 cudaError_t HMCSC_NAME(launch_batch_density)(const BatchArgs &a, cudaStream_t s) {
   k_batch_density<kST><<<(unsigned)a.prefix[a.n], dim3(kTile, kBatchBY, 1), 0, s>>>(a);
   return cudaGetLastError();

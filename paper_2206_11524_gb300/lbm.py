@@ -37,9 +37,10 @@ ABI_SYMBOLS = (
     "lbm_save", "lbm_load", "lbm_last_error", "lbm_reduce_fields_noalloc",
     "lbm_batch_step", "lbm_batch_graph_create", "lbm_batch_graph_launch",
     "lbm_batch_graph_destroy", "lbm_set_launch_config",
-    "lbm_set_geometry_per_component", "lbm_set_bc_velocity",
+    "lbm_set_geometry_per_component", "lbm_set_bc_velocity", "lbm_set_single_pass",
 )
 LBM_DENSITY_CONFIGS, LBM_COLLIDE_CONFIGS = 3, 4
+SINGLE_PASS_MAX_NX = 256
 LBM_BATCH_MAX = 64
 
 
@@ -95,6 +96,7 @@ def load(path: str | None = None):
         "lbm_set_bc": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double]),
         "lbm_set_bc_velocity": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int] + [ctypes.c_double] * 5),
         "lbm_step": (ctypes.c_int, [vp, ctypes.c_int]),
+        "lbm_set_single_pass": (ctypes.c_int, [vp, ctypes.c_int]),
         "lbm_density": (ctypes.c_int, [vp]),
         "lbm_collide_stream": (ctypes.c_int, [vp]),
         "lbm_time": (ctypes.c_int64, [vp]),
@@ -204,6 +206,10 @@ def lbm_set_bc_velocity(ctx, face, layers, rho_a, rho_b, ux, uy, uz):
 
 def lbm_step(ctx, n_steps):
     return _check(ctx, load().lbm_step(ctx, int(n_steps)))
+
+
+def lbm_set_single_pass(ctx, planes):
+    return _check(ctx, load().lbm_set_single_pass(ctx, int(planes)))
 
 
 def lbm_density(ctx):
@@ -392,14 +398,19 @@ class Lattice:
     def step(self, n=1):
         lbm_step(self.ctx, n)
 
+    def set_single_pass(self, planes):
+        """Single-pass lbm_step with boxes of `planes` planes (0: two passes)."""
+        lbm_set_single_pass(self.ctx, planes)
+
     def set_launch_config(self, density_cfg=0, even_cfg=0, odd_cfg=0):
         lbm_set_launch_config(self.ctx, density_cfg, even_cfg, odd_cfg)
 
-    def autotune(self, table=None):
+    def autotune(self, table=None, single_pass=False):
         """Launch shapes for this size and storage from the tuning table
-        (timed on a scratch lattice first if the table has none)."""
+        (timed on a scratch lattice first if the table has none); with
+        single_pass the tuner also weighs the single-pass step."""
         from . import autotune
-        return autotune.apply(self, table)
+        return autotune.apply(self, table, single_pass=single_pass)
 
     @property
     def t(self):

@@ -139,10 +139,19 @@ class _Slot:
 
 
 class Server:
-    """Continuous batching of resident simulations on the current GPU."""
+    """Continuous batching of resident simulations on the current GPU.
+
+    Every admitted simulation is resident; each tick advances a batch of them
+    together.  `fill_nodes` sets which: the oldest resident requests, in
+    arrival order, until their lattices hold at least `fill_nodes` nodes (the
+    size at which one batch keeps the GPU busy), so a large old request runs
+    nearly alone while small ones are batched; fill_nodes = None advances
+    every resident request each tick (processor sharing, which stretches the
+    largest requests' latency by the number of requests beside them)."""
 
     def __init__(self, storage="f16l", tick_steps=400, use_graphs=True,
-                 max_batch=lbm.LBM_BATCH_MAX, hbm_budget=None, keep_state=False):
+                 max_batch=lbm.LBM_BATCH_MAX, hbm_budget=None, keep_state=False,
+                 fill_nodes=1 << 23):
         import torch
         self.torch = torch
         self.storage = storage
@@ -153,6 +162,7 @@ class Server:
         self.budget = int(hbm_budget if hbm_budget is not None else 0.8 * free)
         self.stream = torch.cuda.Stream()
         self.keep_state = keep_state
+        self.fill_nodes = fill_nodes
         self._graphs = {}
         self.ticks = 0
         self.graph_launches = 0
@@ -169,6 +179,20 @@ class Server:
             active.append(_Slot(req, lat, req.steps, now))
             used += need
         return used
+
+    def _batch(self, active):
+        """Requests advanced this tick (active is in arrival order)."""
+        if self.fill_nodes is None:
+            return active
+        batch, nodes = [], 0
+        for s in active:
+            if s.remaining <= 0:
+                continue
+            batch.append(s)
+            nodes += s.req.nodes
+            if nodes >= self.fill_nodes:
+                break
+        return batch
 
     def _graph(self, slots, K):
         key = (tuple(s.req.rid for s in slots), K)
@@ -198,17 +222,18 @@ class Server:
                 time.sleep(max(0.0, pending[0].arrival - now()))
                 used = self._admit(pending, active, used, now())
                 continue
+            batch = self._batch(active)
             # Newly admitted lattices first take two plain batched steps: a
             # graph needs their reservoirs in force, and two steps keep the
             # remaining budget even.
-            fresh = [s for s in active if not s.stepped]
+            fresh = [s for s in batch if not s.stepped]
             if fresh:
                 n = min(2, min(s.remaining for s in fresh))
                 lbm.lbm_batch_step([s.lat.ctx for s in fresh], n, self.stream.cuda_stream)
                 for s in fresh:
                     s.stepped = True
                     s.remaining -= n
-            ctxs = [s for s in active if s.remaining > 0]
+            ctxs = [s for s in batch if s.remaining > 0]
             K = min([self.tick_steps] + [s.remaining for s in ctxs]) if ctxs else 0
             if ctxs and K > 0:
                 # a graph runs an even number of steps; an odd tail is stepped plainly
@@ -275,3 +300,36 @@ def summarize(results):
             "p99_s": float(np.percentile(lat, 99)),
             "makespan_s": end - start,
             "mlups": work / (end - start) / 1e6}
+
+
+def compare(n_req=24, L_min=32, L_max=160, steps_min=1000, steps_max=6000,
+            storage="f16l", load=0.9, seed=2206, tick_steps=400):
+    """Continuous batching against one-at-a-time float32 runs on the same
+    seeded trace, offered at `load` x the sequential capacity (measured on
+    three median-size requests of the trace): the arrival times are Poisson
+    at that rate.  Returns both summaries and the trace description."""
+    reqs = make_requests(n_req=n_req, seed=seed, L_min=L_min, L_max=L_max,
+                         steps_min=steps_min, steps_max=steps_max, base_n=L_max)
+    work = [r.nodes * r.steps for r in reqs]
+    probe = sorted(reqs, key=lambda r: r.nodes)[len(reqs) // 2 - 1: len(reqs) // 2 + 2]
+    for r in probe:
+        r.arrival = 0.0
+    cal = summarize(run_sequential(probe))
+    rate = load * cal["mlups"] * 1e6 / (sum(work) / len(work))
+    rng = np.random.default_rng(seed + 1)
+    t = 0.0
+    for r in reqs:
+        t += float(rng.exponential(1.0 / rate))
+        r.arrival = t
+    seq = summarize(run_sequential(reqs))
+    srv = Server(storage=storage, tick_steps=tick_steps)
+    bat = summarize(srv.run(reqs))
+    bat.update(storage=storage, graph_launches=srv.graph_launches,
+               captures=srv.captures, ticks=srv.ticks)
+    seq.update(storage="f32")
+    return {"trace": f"{len(reqs)} requests, cubic L in [{L_min}, {L_max}] "
+                     f"log-uniform, steps U{{{steps_min}..{steps_max}}}, Poisson "
+                     f"arrivals at {load} x sequential capacity ({rate:.3f}/s), "
+                     "seeded electrode crops with per-request G and binder "
+                     "wettability",
+            "batched": bat, "sequential": seq}

@@ -7,6 +7,13 @@
 `saturation`  imbibition into the synthetic electrode (Sec. 4): the
               saturation curve S_1(t) of Eq. 19 for several population
               storages, each against the float32 run of the same case.
+`relperm`     relative permeabilities of two immiscible fluids in a
+              homogeneous gray medium (Sec. 3.1, Eqs. 9-10): stratified
+              layers of fluid 1 and fluid 2 along the body force.
+`serving`     a stream of independent imbibition requests of different
+              sizes, microstructures and wettabilities: continuous batching
+              in 16-bit storage against one-at-a-time float32 runs (p50 / p99
+              time to result, aggregate MLUPS).
 
 Run as ``python -m paper_2206_11524_gb300.studies <study> [options]``; the
 result is printed and written as JSON to ``--out``.
@@ -126,6 +133,54 @@ def saturation(shape=(256, 256, 256), storages=("f32", "f16", "bf16", "f16l", "b
     return out
 
 
+# D3Q19 x-components in the order of Eq. A.8 (for the momentum of the
+# read-back populations).
+_CX = np.array([0, -1, 0, 0, -1, -1, -1, -1, 0, 0, 1, 0, 0, 1, 1, 1, 1, 0, 0],
+               dtype=np.float64)
+
+
+def component_flux(lat, ns, F):
+    """Mean x-momentum of each component with Eq. 7's weighting,
+    (1 - n_s)(j_sigma + F_sigma / 2), where F_sigma = rho_sigma / rho F_ext
+    along x (the fluid-fluid forces of a flat interface along the flow and
+    the adhesion of a uniform medium have no mean x-component)."""
+    f = lat.populations().astype(np.float64)
+    rho = f.sum(axis=1)                                  # [2, nz, ny, nx]
+    jx = np.tensordot(_CX, f, axes=([0], [1]))           # [2, nz, ny, nx]
+    share = rho / rho.sum(axis=0)
+    return [(1.0 - ns) * float((jx[k] + 0.5 * share[k] * F).mean()) for k in range(2)]
+
+
+def relperm(n=50, ns_values=(0.1, 0.5, 0.9), saturations=(0.0, 0.2, 0.4, 0.6, 0.8, 1.0),
+            steps=3000, F=1e-5, G=1.75):
+    """k_r,sigma(S_1) = k(S_sigma) / k(S_sigma = 1), k = nu <rho_sigma u_sigma>
+    / F_ext (Eqs. 9-10), for stratified layers (fluid 1 in the first S_1 n
+    rows) driven along x, n x n x 1 lattice, tau = 1, G_ads = 0."""
+    nu = 1.0 / 6.0
+    hi, lo = COEXIST_175
+    out = {"study": "relperm", "n": n, "steps": steps, "rows": []}
+    for ns in ns_values:
+        flux = {}
+        for S in saturations:
+            shape = (1, n, n)
+            rows1 = int(round(S * n))
+            y = np.arange(n)[None, :, None] * np.ones(shape)
+            ra = np.where(y < rows1, hi, lo)
+            lat = lbm.Lattice(n, n, 1, tau=(1.0, 1.0), G=G, F_ext=(F, 0.0, 0.0))
+            lat.set_geometry(np.full(shape, ns))
+            lat.init_equilibrium(ra, hi + lo - ra)
+            lat.step(steps)
+            flux[S] = component_flux(lat, ns, F)
+            lat.close()
+        k1_full, k2_full = nu * flux[1.0][0] / F, nu * flux[0.0][1] / F
+        for S in saturations:
+            out["rows"].append({"ns": ns, "S1": S,
+                                "kr1": nu * flux[S][0] / F / k1_full,
+                                "kr2": nu * flux[S][1] / F / k2_full,
+                                "k_single": k1_full})
+    return out
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     sub = ap.add_subparsers(dest="study", required=True)
@@ -141,6 +196,19 @@ def main(argv=None):
     b.add_argument("--every", type=int, default=1000)
     b.add_argument("--storages", default="f32,f16,bf16,f16l,bf16l")
     b.add_argument("--out", default="")
+    d = sub.add_parser("relperm")
+    d.add_argument("--n", type=int, default=50)
+    d.add_argument("--steps", type=int, default=3000)
+    d.add_argument("--out", default="")
+    c = sub.add_parser("serving")
+    c.add_argument("--requests", type=int, default=256)
+    c.add_argument("--lmin", type=int, default=32)
+    c.add_argument("--lmax", type=int, default=192)
+    c.add_argument("--steps-min", type=int, default=5000)
+    c.add_argument("--steps-max", type=int, default=40000)
+    c.add_argument("--storage", default="f16l")
+    c.add_argument("--load", type=float, default=0.9)
+    c.add_argument("--out", default="")
     args = ap.parse_args(argv)
     from . import build
     build.build()
@@ -149,10 +217,18 @@ def main(argv=None):
         res = laplace(n=args.n, steps=args.steps,
                       radii=tuple(int(v) for v in args.radii.split(",")),
                       ns_values=tuple(float(v) for v in args.ns.split(",")))
-    else:
+    elif args.study == "relperm":
+        res = relperm(n=args.n, steps=args.steps)
+    elif args.study == "saturation":
         res = saturation(shape=tuple(int(v) for v in args.shape.split(",")),
                          storages=tuple(args.storages.split(",")),
                          steps=args.steps, every=args.every)
+    else:
+        from . import serve
+        res = serve.compare(n_req=args.requests, L_min=args.lmin, L_max=args.lmax,
+                            steps_min=args.steps_min, steps_max=args.steps_max,
+                            storage=args.storage, load=args.load)
+        res["study"] = "serving"
     text = json.dumps(res, indent=1)
     if args.out:
         with open(args.out, "w") as fh:

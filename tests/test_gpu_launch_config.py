@@ -58,3 +58,24 @@ def test_autotune_records_and_applies(tmp_path):
         g.set_launch_config(0, lbm.LBM_COLLIDE_CONFIGS, 0)
     g.step(2)
     g.close()
+
+
+def test_autotune_weighs_the_single_pass(tmp_path):
+    """With single_pass the table entry gets a fourth value (box depth or 0)
+    and applying it gives the same populations as the defaults."""
+    table = autotune.TuneTable(str(tmp_path / "t.json"))
+    shape = (40, 48, 64)
+    ns, gads = synth.random_geometry(shape, 3)
+    f0 = synth.random_state(shape, 4)
+    out = []
+    for tuned in (False, True):
+        g = lbm.Lattice(64, 48, 40, tau=(0.9, 1.1), G=1.5)
+        g.set_geometry(ns, gads)
+        g.set_populations(f0)
+        if tuned:
+            cfg = g.autotune(table, single_pass=True)
+            assert len(cfg) == 4 and cfg[3] >= 0
+        g.step(3)
+        out.append(g.populations())
+        g.close()
+    assert np.array_equal(out[0], out[1])

@@ -434,3 +434,26 @@ def test_couette_profile_matches_oracle_and_eq14():
     ua = U0 * np.sinh(r_ * np.arange(nx)) / math.sinh(r_ * H)
     assert np.abs(ug - ua).max() <= 0.03 * U0
     g.close()
+
+
+def test_relative_permeability_stratified_layers():
+    """Relative permeabilities (Sec. 3.1, Eqs. 9-10) of stratified layers in
+    a homogeneous medium: both fluids have the properties of Table 1, so
+    k_r,1(S_1) = k_r,2(1 - S_1), the trend is almost linear and hardly
+    depends on n_s (the paper's observations); with fluid 1 alone, its k is
+    Eq. 2 times its share of the density (0.965: fluid 2 stays dissolved at
+    the coexistence value), since both components share u^eq (Eq. 6)."""
+    from paper_2206_11524_gb300 import params, studies
+    res = studies.relperm(n=40, ns_values=(0.1, 0.9), saturations=(0.0, 0.25, 0.5, 0.75, 1.0),
+                          steps=1500)
+    by = {(r["ns"], r["S1"]): r for r in res["rows"]}
+    for ns in (0.1, 0.9):
+        k = by[(ns, 1.0)]["k_single"]
+        share = studies.COEXIST_175[0] / sum(studies.COEXIST_175)
+        assert abs(k / (share * params.permeability(ns)) - 1) < 0.01, (ns, k)
+        for S in (0.25, 0.5, 0.75):
+            r, m = by[(ns, S)], by[(ns, round(1 - S, 2))]
+            assert abs(r["kr1"] - m["kr2"]) < 0.02, (ns, S)
+            assert abs(r["kr1"] - S) < 0.1, (ns, S, r["kr1"])
+    for S in (0.25, 0.5, 0.75):
+        assert abs(by[(0.1, S)]["kr1"] - by[(0.9, S)]["kr1"]) < 0.1
