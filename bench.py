@@ -50,6 +50,7 @@ BYTES_COLLIDE = 320
 STORAGE_BYTES = {"f32": (160, 320), "f16": (84, 168), "bf16": (84, 168),
                  "f16l": (92, 176), "bf16l": (92, 176)}
 FALLBACK_HBM_GBS = 6800.0
+NOMINAL_HBM_GBS = 8000.0   # GB300 HBM3e nominal, for context only
 
 
 def _peaks():
@@ -337,6 +338,7 @@ def run_gpu(args, world, rank, local):
     d2h = 6 * 4 * N
 
     peak, peak_kind = _peaks()
+    step_gbs = (bytes_density + bytes_collide) * N / (ms_max / K / 1e3) / 1e9
     dims = f"{nx}^3" if nx == ny == nz else f"{nx}x{ny}x{nz}"
     achieved = bytes_collide * N / (ms_collide / 1e3) / 1e9
     traffic_bpn = _profiled_traffic("collide_stream") if storage == "f32" else None
@@ -374,7 +376,10 @@ def run_gpu(args, world, rank, local):
                      "algorithmic_bytes_per_node": bytes_collide,
                      "traffic": (traffic_bpn * N if traffic_bpn else None)},
         "kernels_ms": {"density": ms_density, "collide_stream": ms_collide},
-        "step_hbm_gbs": (bytes_density + bytes_collide) * N / (ms_max / K / 1e3) / 1e9,
+        "step_hbm_gbs": step_gbs,
+        "step_frac": step_gbs / peak,
+        "frac_of_nominal_8tbs": {"fused_pass": achieved / NOMINAL_HBM_GBS,
+                                 "step": step_gbs / NOMINAL_HBM_GBS},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d / K,
                 "d2h_bytes_per_step": d2h / K},
         "gpu_launches": 2 * K,   # density pass + fused pass per step
