@@ -63,6 +63,14 @@ def _peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
+def _seam_nodes(nx, ny, nz, planes, box_rows=8):
+    """Nodes of the single-pass seams: the last row of every box of
+    box_rows rows and the last plane of every run of about `planes` planes."""
+    nzc = max(1, min(nz, (nz + planes // 2) // planes))
+    seam_rows = (ny + box_rows - 1) // box_rows
+    return nx * (seam_rows * nz + (ny - seam_rows) * nzc)
+
+
 def _kernel_sha():
     h = hashlib.sha256()
     for f in ("lbm_device.cuh", "lbm_internal.cuh", "lbm_storage_impl.cuh"):
@@ -279,9 +287,15 @@ def run_gpu(args, world, rank, local):
         table = autotune.TuneTable(os.path.join(tempfile.mkdtemp(), "launch_table.json"))
         launch = list(lat.autotune(table))
 
+    single = args.single_pass > 0
+    if single:
+        lat.set_single_pass(args.single_pass)
     for _ in range(args.warmup):
-        lbm.lbm_density(ctx)
-        lbm.lbm_collide_stream(ctx)
+        if single:
+            lbm.lbm_step(ctx, 1)
+        else:
+            lbm.lbm_density(ctx)
+            lbm.lbm_collide_stream(ctx)
     torch.cuda.synchronize()
 
     K = args.steps
@@ -298,9 +312,13 @@ def run_gpu(args, world, rank, local):
     for k in range(K):
         e0, e1, e2 = ev[k]
         e0.record(stream)
-        lbm.lbm_density(ctx)
+        if single:
+            lbm.lbm_step(ctx, 1)   # bulk sweep + seam launches
+        else:
+            lbm.lbm_density(ctx)
         e1.record(stream)
-        lbm.lbm_collide_stream(ctx)
+        if not single:
+            lbm.lbm_collide_stream(ctx)
         e2.record(stream)
     stop.record(stream)
     torch.cuda.synchronize()
@@ -338,10 +356,22 @@ def run_gpu(args, world, rank, local):
     d2h = 6 * 4 * N
 
     peak, peak_kind = _peaks()
-    step_gbs = (bytes_density + bytes_collide) * N / (ms_max / K / 1e3) / 1e9
     dims = f"{nx}^3" if nx == ny == nz else f"{nx}x{ny}x{nz}"
-    achieved = bytes_collide * N / (ms_collide / 1e3) / 1e9
-    traffic_bpn = _profiled_traffic("collide_stream") if storage == "f32" else None
+    if single:
+        # whole single-pass step: every node 320 B as in the fused pass, and
+        # the density pass's 160 B again only for the seam nodes
+        n_seam = _seam_nodes(nx, ny, nz, args.single_pass)
+        kernel_name = "single-pass step (k_sp_bulk + k_sp_seams)"
+        bytes_launch = bytes_collide * N + bytes_density * n_seam
+        achieved = bytes_launch / (ms_density / 1e3) / 1e9
+        traffic_bpn = None
+        step_gbs = bytes_launch / (ms_max / K / 1e3) / 1e9
+    else:
+        step_gbs = (bytes_density + bytes_collide) * N / (ms_max / K / 1e3) / 1e9
+        kernel_name = "k_collide_stream"
+        bytes_launch = bytes_collide * N
+        achieved = bytes_collide * N / (ms_collide / 1e3) / 1e9
+        traffic_bpn = _profiled_traffic("collide_stream") if storage == "f32" else None
     if rank != 0:
         return 0
     serving = None
@@ -372,17 +402,19 @@ def run_gpu(args, world, rank, local):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak,
                      "peak_kind": f"{peak_kind} hbm_gbs",
-                     "kernel": "k_collide_stream",
-                     "algorithmic_bytes_per_node": bytes_collide,
+                     "kernel": kernel_name,
+                     "algorithmic_bytes_per_node": bytes_launch / N,
                      "traffic": (traffic_bpn * N if traffic_bpn else None)},
-        "kernels_ms": {"density": ms_density, "collide_stream": ms_collide},
+        "kernels_ms": ({"single_pass_step": ms_density} if single else
+                       {"density": ms_density, "collide_stream": ms_collide}),
         "step_hbm_gbs": step_gbs,
         "step_frac": step_gbs / peak,
         "frac_of_nominal_8tbs": {"fused_pass": achieved / NOMINAL_HBM_GBS,
                                  "step": step_gbs / NOMINAL_HBM_GBS},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d / K,
                 "d2h_bytes_per_step": d2h / K},
-        "gpu_launches": 2 * K,   # density pass + fused pass per step
+        # density pass + fused pass per step, or bulk sweep + 2 seam launches
+        "gpu_launches": (3 if single else 2) * K,
         "clocks": clk,
         "cpu_baseline": cpu,
         "serving": serving,
@@ -407,6 +439,8 @@ def main(argv=None):
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--single-pass", type=int, default=0,
+                    help="time the single-pass step with boxes of about this many planes")
     ap.add_argument("--launch-config", default="",
                     help="density,even,odd launch shapes (skips the autotuner)")
     ap.add_argument("--serve-requests", type=int, default=24)
