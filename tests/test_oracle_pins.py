@@ -623,3 +623,75 @@ def test_couette_brinkman_profile_eq14(ns):
     err = np.abs(u - ua)
     assert err.max() <= 0.03 * U0, err.max() / U0
     assert err[x <= 0.9 * H].max() <= 0.005 * U0
+
+
+# --------------------------------------------------------------------------
+# Washburn imbibition (Sec. 3.4, Eq. 16, Table 3)
+# --------------------------------------------------------------------------
+
+def _washburn_front(gads, ns, H=500, steps=50000, samples=20):
+    """Imbibition along x into a homogeneous gray medium (n_s, G_ads uniform)
+    between an inlet reservoir of fluid 1 (x = 0..3) and an outlet reservoir
+    of fluid 2 (x = H-4..H-1), the reservoir layers free of medium; the
+    domain is uniform across y (periodic), so one row suffices.  Returns
+    sample times and the interface position (rho_1 = 0.5, interpolated)
+    measured from the medium's face."""
+    res = {0: (4, 0.99, 0.01), 1: (4, 0.01, 0.99)}
+    p = oracle.Params(H, 1, 1, tau=(1.0, 1.0), G=1.75, reservoirs=res)
+    x = np.arange(H)
+    medium = (x >= 4) & (x < H - 4)
+    s = oracle.Sim(p, np.where(medium, ns, 0.0)[None, None],
+                   np.where(medium, gads, 0.0)[None, None])
+    ra = np.where(x < 4, 0.99, 0.01)[None, None] * 1.0
+    rb = np.where(x < 4, 0.01, 0.99)[None, None] * 1.0
+    s.init_equilibrium(ra, rb)
+    ts, xs = [], []
+    for _ in range(samples):
+        s.step(steps // samples)
+        r1 = s.f[0].sum(axis=0)[0, 0]
+        pos = 0.0
+        for k in range(4, H - 5):
+            if r1[k] >= 0.5 > r1[k + 1]:
+                pos = k - 4 + 0.5 + (r1[k] - 0.5) / (r1[k] - r1[k + 1])
+                break
+        ts.append(s.t)
+        xs.append(pos)
+    return np.array(ts, float), np.array(xs)
+
+
+def _washburn_fit(ts, xs):
+    """x^2 = a t through the origin (Eq. 16 squared: a = A^2 B) and the R^2
+    of x against its fit."""
+    a = float((xs ** 2) @ ts / (ts @ ts))
+    fit = np.sqrt(a * ts)
+    r2 = 1 - ((xs - fit) ** 2).sum() / ((xs - xs.mean()) ** 2).sum()
+    return a, r2
+
+
+@pytest.mark.slow
+def test_washburn_fronts_follow_table3():
+    """Reading of the garbled set-up (H = 500 lu of medium with reservoirs at
+    both ends, imbibition along x, uniform n_s and G_ads): the front follows
+    x ~ sqrt(t) (R^2 > 0.97, the paper's criterion), and Eq. 16 fitted the
+    paper's way reproduces Table 3 -- A (with B held at the table's
+    R_eff(0.5)) within 10 % for G_ads = 0.05, 0.2, 0.4 at n_s = 0.5, and B
+    (with A held at the table's A(0.2)) within 10 % for n_s = 0.1 and 20 %
+    for n_s = 0.9, the fit the paper rates lowest (R_B^2 = 0.972).  An
+    adhesion force of the wrong sign or taken at the wrong node stops or
+    reverses the front; a slip in Eq. 2's permeability moves B."""
+    t3 = _golden("washburn_fits_table3.txt")
+    A_tab = {round(g, 2): v for k, g, v in t3 if k == 0}
+    B_tab = {round(n, 2): v for k, n, v in t3 if k == 1}
+    A_prev = 0.0
+    for gads in (0.05, 0.2, 0.4):
+        a, r2 = _washburn_fit(*_washburn_front(gads, 0.5))
+        A = math.sqrt(a / B_tab[0.5])
+        assert r2 > 0.97, (gads, r2)
+        assert abs(A / A_tab[gads] - 1) < 0.10, (gads, A, A_tab[gads])
+        assert A > A_prev
+        A_prev = A
+    for ns, tol in ((0.1, 0.10), (0.9, 0.20)):
+        a, r2 = _washburn_fit(*_washburn_front(0.2, ns))
+        B = a / A_tab[0.2] ** 2
+        assert r2 > 0.97, (ns, r2)
+        assert abs(B / B_tab[ns] - 1) < tol, (ns, B, B_tab[ns])
