@@ -10,6 +10,9 @@
 `relperm`     relative permeabilities of two immiscible fluids in a
               homogeneous gray medium (Sec. 3.1, Eqs. 9-10): stratified
               layers of fluid 1 and fluid 2 along the body force.
+`washburn`    capillary imbibition into a homogeneous gray medium (Sec. 3.4,
+              Eq. 16, Table 3): the front position against time for the
+              paper's G_ads and n_s series, fitted as x = A sqrt(B t).
 `serving`     a stream of independent imbibition requests of different
               sizes, microstructures and wettabilities: continuous batching
               in 16-bit storage against one-at-a-time float32 runs (p50 / p99
@@ -181,6 +184,72 @@ def relperm(n=50, ns_values=(0.1, 0.5, 0.9), saturations=(0.0, 0.2, 0.4, 0.6, 0.
     return out
 
 
+def washburn_setup(gads, ns, H=500, storage="f32"):
+    """Imbibition along x through H lu: an inlet reservoir of fluid 1
+    (x = 0..3), uniform gray medium (n_s, G_ads) in between, an outlet
+    reservoir of fluid 2 (x = H-4..H-1), the reservoir layers free of
+    medium; uniform across y, so one row (periodic) suffices.  This reads the
+    paper's set-up (Sec. 3.4), whose axes are garbled in the text."""
+    x = np.arange(H)
+    medium = (x >= 4) & (x < H - 4)
+    lat = lbm.Lattice(H, 1, 1, tau=(1.0, 1.0), G=1.75, storage=storage,
+                      rho0=(0.5, 0.5))
+    lat.set_geometry(np.where(medium, ns, 0.0)[None, None],
+                     np.where(medium, gads, 0.0)[None, None])
+    lat.set_bc(0, 4, 0.99, 0.01)
+    lat.set_bc(1, 4, 0.01, 0.99)
+    ra = np.where(x < 4, 0.99, 0.01)[None, None] * 1.0
+    lat.init_equilibrium(ra, 1.0 - ra)
+    return lat
+
+
+def front_position(rho1, x0=4):
+    """Where rho_1 falls through 0.5 behind the inlet (linear interpolation),
+    measured from the medium's face at x0; 0 before the front enters."""
+    for k in range(x0, len(rho1) - 1):
+        if rho1[k] >= 0.5 > rho1[k + 1]:
+            return k - x0 + 0.5 + (rho1[k] - 0.5) / (rho1[k] - rho1[k + 1])
+    return 0.0
+
+
+def washburn_front(gads, ns, H=500, steps=50000, samples=20):
+    lat = washburn_setup(gads, ns, H)
+    ts, xs = [], []
+    for _ in range(samples):
+        lat.step(steps // samples)
+        ts.append(lat.t)
+        xs.append(front_position(lat.fields()["rho_a"][0, 0]))
+    lat.close()
+    return np.array(ts, float), np.array(xs)
+
+
+def washburn(gads_values=(0.05, 0.10, 0.15, 0.20, 0.25, 0.30, 0.35, 0.40),
+             ns_values=(0.1, 0.5, 0.9), H=500, steps=50000):
+    """Table 3's two series: n_s = 0.5 with G_ads varied, and G_ads = 0.2
+    with n_s varied.  Eq. 16 squared, x^2 = A^2 B t, is fitted through the
+    origin (a = A^2 B); the paper holds B in the first series and A in the
+    second, so both a and R^2 (of x against sqrt(a t)) are reported."""
+    out = {"study": "washburn", "H": H, "steps": steps, "gads_series": [],
+           "ns_series": []}
+
+    def fit(ts, xs):
+        a = float((xs ** 2) @ ts / (ts @ ts))
+        r2 = 1 - float(((xs - np.sqrt(a * ts)) ** 2).sum() / ((xs - xs.mean()) ** 2).sum())
+        return a, r2
+
+    for g in gads_values:
+        ts, xs = washburn_front(g, 0.5, H, steps)
+        a, r2 = fit(ts, xs)
+        out["gads_series"].append({"gads": g, "ns": 0.5, "a": a, "r2": r2,
+                                   "x_final": float(xs[-1])})
+    for n in ns_values:
+        ts, xs = washburn_front(0.2, n, H, steps)
+        a, r2 = fit(ts, xs)
+        out["ns_series"].append({"gads": 0.2, "ns": n, "a": a, "r2": r2,
+                                 "x_final": float(xs[-1])})
+    return out
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     sub = ap.add_subparsers(dest="study", required=True)
@@ -196,6 +265,9 @@ def main(argv=None):
     b.add_argument("--every", type=int, default=1000)
     b.add_argument("--storages", default="f32,f16,bf16,f16l,bf16l")
     b.add_argument("--out", default="")
+    e = sub.add_parser("washburn")
+    e.add_argument("--steps", type=int, default=50000)
+    e.add_argument("--out", default="")
     d = sub.add_parser("relperm")
     d.add_argument("--n", type=int, default=50)
     d.add_argument("--steps", type=int, default=3000)
@@ -217,6 +289,8 @@ def main(argv=None):
         res = laplace(n=args.n, steps=args.steps,
                       radii=tuple(int(v) for v in args.radii.split(",")),
                       ns_values=tuple(float(v) for v in args.ns.split(",")))
+    elif args.study == "washburn":
+        res = washburn(steps=args.steps)
     elif args.study == "relperm":
         res = relperm(n=args.n, steps=args.steps)
     elif args.study == "saturation":

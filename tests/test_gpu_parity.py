@@ -457,3 +457,31 @@ def test_relative_permeability_stratified_layers():
             assert abs(r["kr1"] - S) < 0.1, (ns, S, r["kr1"])
     for S in (0.25, 0.5, 0.75):
         assert abs(by[(0.1, S)]["kr1"] - by[(0.9, S)]["kr1"]) < 0.1
+
+
+def test_washburn_front_matches_oracle_and_table3():
+    """The Washburn imbibition of Sec. 3.4 (see studies.washburn_setup): the
+    GPU front position equals the oracle's over 10,000 steps (to 0.05 lu),
+    and over the paper's 50,000 steps Eq. 16 fitted as in Table 3 gives A
+    within 10 % of the table for G_ads = 0.05 and 0.4 (n_s = 0.5)."""
+    from paper_2206_11524_gb300 import studies
+    H, steps = 500, 10000
+    ts_g, xs_g = studies.washburn_front(0.2, 0.5, H, steps, samples=5)
+    x = np.arange(H)
+    medium = (x >= 4) & (x < H - 4)
+    res = {0: (4, float(np.float32(0.99)), float(np.float32(0.01))),
+           1: (4, float(np.float32(0.01)), float(np.float32(0.99)))}
+    r = oracle.Sim(oracle.Params(H, 1, 1, tau=(1.0, 1.0), G=1.75, reservoirs=res),
+                   w64(np.where(medium, 0.5, 0.0)[None, None]),
+                   w64(np.where(medium, 0.2, 0.0)[None, None]))
+    ra = np.where(x < 4, 0.99, 0.01)[None, None] * 1.0
+    r.init_equilibrium(w64(ra), w64(1.0 - ra))
+    for k in range(5):
+        r.step(steps // 5)
+        xr = studies.front_position(r.fields()["rho_a"][0, 0])
+        assert abs(xs_g[k] - xr) < 0.05, (k, xs_g[k], xr)
+    table = {0.05: 0.275, 0.4: 0.463}   # Table 3, B held at 0.0481
+    for gads, A_tab in table.items():
+        ts, xs = studies.washburn_front(gads, 0.5, H, 50000)
+        a = float((xs ** 2) @ ts / (ts @ ts))
+        assert abs(math.sqrt(a / 0.0481) / A_tab - 1) < 0.10, gads
