@@ -196,6 +196,30 @@ def cpu_oracle_mlups(case_small, budget_s: float, max_steps: int | None = None):
     return case_small.n_nodes * steps / el / 1e6, steps, el
 
 
+def _single_core_oracle(seconds):
+    """The same oracle sample on one host core (a child process started with
+    OMP_NUM_THREADS=1, since the thread count is fixed when the library
+    loads)."""
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    try:
+        out = subprocess.run([sys.executable, os.path.abspath(__file__),
+                              "--cpu-probe", str(seconds)], env=env,
+                             capture_output=True, text=True, timeout=300)
+        return json.loads(out.stdout.strip().splitlines()[-1])
+    except Exception as e:  # the single-core figure is context only
+        return {"unavailable": str(e)[:200]}
+
+
+def _cpu_probe(seconds):
+    from paper_2206_11524_gb300 import synth
+    small = synth.electrode((64, 64, 64))
+    mlups, st, el = cpu_oracle_mlups(small, seconds)
+    print(json.dumps({"value": mlups, "unit": UNIT, "cores": 1,
+                      "sample": f"64^3 synthetic electrode, {st} FP64 time "
+                                f"steps in {el:.1f} s"}), flush=True)
+    return 0
+
+
 def _cores():
     n = os.environ.get("OMP_NUM_THREADS")
     return int(n) if n else (os.cpu_count() or 1)
@@ -383,7 +407,8 @@ def run_gpu(args, world, rank, local):
         mlups, st, el = cpu_oracle_mlups(small, args.cpu_seconds)
         cpu = {"value": mlups, "unit": UNIT, "cores": _cores(), "kind": "oracle",
                "sample": f"64^3 crop-size synthetic electrode, {st} FP64 "
-                         f"time steps in {el:.1f} s"}
+                         f"time steps in {el:.1f} s",
+               "single_core": _single_core_oracle(args.cpu_seconds / 3)}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": K, "warmup": args.warmup, "ms_per_step": ms_max / K,
@@ -447,7 +472,10 @@ def main(argv=None):
     ap.add_argument("--serve-lmax", type=int, default=160)
     ap.add_argument("--serve-steps-max", type=int, default=6000)
     ap.add_argument("--serve-storage", default="f16l")
+    ap.add_argument("--cpu-probe", type=float, default=0.0, help=argparse.SUPPRESS)
     args = ap.parse_args(argv)
+    if args.cpu_probe > 0:
+        return _cpu_probe(args.cpu_probe)
     world, rank, local = _dist()
     if args.impl == "reference":
         return run_reference(args, world, rank)
