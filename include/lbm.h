@@ -259,6 +259,19 @@ LBM_API lbm_status lbm_batch_graph_create(lbm_ctx *const *ctxs, int n,
 LBM_API lbm_status lbm_batch_graph_launch(lbm_graph *graph, void *cuda_stream);
 LBM_API void lbm_batch_graph_destroy(lbm_graph *graph);
 
+/* ---- Bounds-checked builds -------------------------------------------------
+ * The library can be compiled with -DHMCSC_CHECKED (build.build(checked=True)):
+ * every population, density, geometry, staging and shared-memory index is
+ * then tested before the access, and an index out of range sets a bit in a
+ * fault word kept in the workspace (1 population load, 2 population store,
+ * 4 density load, 8 density store, 16 geometry, 32 shared ring, 64 staging)
+ * instead of being used.  lbm_build_checked() returns 1 in such a build, 0
+ * otherwise.  lbm_fault_word copies the word to *out after waiting for the
+ * context's stream, and zeroes it when clear != 0; in a default build it
+ * stays 0.  Errors: EINVAL (NULL), ECUDA. */
+LBM_API int lbm_build_checked(void);
+LBM_API lbm_status lbm_fault_word(lbm_ctx *ctx, uint32_t *out, int clear);
+
 /* ---- Allocation-free observables -----------------------------------------
  * The paper has no counterpart to this entry point: it exists for callers
  * that cannot call cudaMalloc where they need the observables -- a host

@@ -879,6 +879,22 @@ lbm_status lbm_set_launch_config(lbm_ctx *c, int density_cfg, int even_cfg,
   return LBM_OK;
 }
 
+int lbm_build_checked(void) { return hmcsc::kChecked ? 1 : 0; }
+
+lbm_status lbm_fault_word(lbm_ctx *c, uint32_t *out, int clear) {
+  if (!c) return LBM_EINVAL;
+  if (!out) return fail(c, LBM_EINVAL, "out is NULL");
+  unsigned v = 0;
+  cudaError_t e = cudaMemcpyAsync(&v, c->ws.fault, sizeof v, cudaMemcpyDeviceToHost,
+                                  c->stream);
+  if (e == cudaSuccess && clear) e = cudaMemsetAsync(c->ws.fault, 0, sizeof v, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "fault word");
+  lbm_status st = sync_stream(c, "fault word");
+  if (st) return st;
+  *out = v;
+  return LBM_OK;
+}
+
 const char *lbm_last_error(const lbm_ctx *c) {
   return c ? c->err.c_str() : "context is NULL";
 }

@@ -74,14 +74,6 @@ __device__ __forceinline__ Geo make_geo(const StepParams &p, int x, int y,
   return g;
 }
 
-// Lane-adjusted base of the tile holding node x + (dx, dy, dz): the pair of
-// slot i of that node is at base[i * 32].
-template <typename T>
-__device__ __forceinline__ T *pop_base(T *f, const Geo &g, int dx, int dy,
-                                       int dz) {
-  return f + g.pop_off(dx, dy, dz);
-}
-
 // Decode references of population i of node x (both components): w_i times
 // the node's own previous density (*_LOCAL) or the constants (*_OFFSET).
 // The product is rounded on its own (no contraction) so that the host
@@ -102,14 +94,21 @@ __device__ __forceinline__ void load_pops(const StepParams &p, const Workspace &
                                           float (&v2)[kQ]) {
   using C = Codec2<ST>;
   const typename C::T2 *f = static_cast<const typename C::T2 *>(w.f);
-  const float2 own_prev = storage_local(ST) ? __ldg(&w.rho_enc[g.node(0, 0, 0)])
-                                            : make_float2(0.f, 0.f);
+  const long long nodes = p.ntiles * kTile, pairs = p.ntiles * kTilePairs;
+  const int own = g.node(0, 0, 0);
+  const float2 own_prev =
+      storage_local(ST)
+          ? __ldg(&w.rho_enc[(kChecked && !in_bounds(w.fault, own, nodes, kFaultRhoLoad)) ? 0 : own])
+          : make_float2(0.f, 0.f);
 #pragma unroll
   for (int i = 0; i < kQ; ++i) {
     // population i of node x: slot i at x (even), slot opp(i) at x - c_i (odd)
-    const typename C::T2 raw =
-        PARITY == 0 ? pop_base(f, g, 0, 0, 0)[i * kTile]
-                    : pop_base(f, g, -cx(i), -cy(i), -cz(i))[opp(i) * kTile];
+    const int slot = PARITY == 0 ? i : opp(i);
+    const typename C::T2 *src =
+        f + (PARITY == 0 ? g.pop_off(0, 0, 0) : g.pop_off(-cx(i), -cy(i), -cz(i)));
+    if (kChecked && !in_bounds(w.fault, (src - f) + slot * kTile, pairs, kFaultPopLoad))
+      src = f - slot * kTile;  // reads element 0
+    const typename C::T2 raw = src[slot * kTile];
     const float2 v = C::dec(raw, dec_ref<ST>(p, own_prev, i));
     v1[i] = v.x;
     v2[i] = v.y;
@@ -151,13 +150,23 @@ __device__ __forceinline__ float2 ld_late(const float2 *ptr) {
 struct GlobalRho {  // the density array written by the density pass
   const float2 *__restrict__ rho;
   const Geo &g;
+  long long nodes;   // tiled nodes (bounds-checked builds)
+  unsigned *fault;
+  __device__ __forceinline__ int idx(int dx, int dy, int dz) const {
+    const int n = g.node(dx, dy, dz);
+    return (kChecked && !in_bounds(fault, n, nodes, kFaultRhoLoad)) ? 0 : n;
+  }
   __device__ __forceinline__ float2 at(int dx, int dy, int dz) const {
-    return __ldg(&rho[g.node(dx, dy, dz)]);
+    return __ldg(&rho[idx(dx, dy, dz)]);
   }
   __device__ __forceinline__ float2 late(int dx, int dy, int dz) const {
-    return ld_late(&rho[g.node(dx, dy, dz)]);
+    return ld_late(&rho[idx(dx, dy, dz)]);
   }
 };
+__device__ __forceinline__ GlobalRho global_rho(const StepParams &p, const Workspace &w,
+                                                const Geo &g) {
+  return GlobalRho{w.rho, g, p.ntiles * kTile, w.fault};
+}
 
 // Total force per unit mass of each component, F_tot,sigma / rho_sigma
 // (Eqs. 3-5; rho_sigma cancels against the prefactor of Eqs. 3-4 and the
@@ -170,16 +179,22 @@ struct GlobalRho {  // the density array written by the density pass
 // summed as pairs, so a uniform field gives exactly zero.
 template <bool PC, typename RS>
 __device__ __forceinline__ void force_per_mass(const StepParams &p, const RS &rs,
-                                               const float *__restrict__ ads,
-                                               const float *__restrict__ ads2,
-                                               const Geo &g, float rho_tot,
-                                               float (&g1)[3], float (&g2)[3]) {
+                                               const Workspace &w, const Geo &g,
+                                               float rho_tot, float (&g1)[3],
+                                               float (&g2)[3]) {
+  const float *__restrict__ ads = w.ads;
+  const float *__restrict__ ads2 = w.ads2;
+  const long long nodes = p.ntiles * kTile;
   float s1[3] = {0.f, 0.f, 0.f}, s2[3] = {0.f, 0.f, 0.f};
   float sa[3] = {0.f, 0.f, 0.f}, sb[3] = {0.f, 0.f, 0.f};
 #pragma unroll
   for (int i = 1; i <= 9; ++i) {
-    const int mp = g.node(cx(i), cy(i), cz(i));
-    const int mm = g.node(-cx(i), -cy(i), -cz(i));
+    int mp = g.node(cx(i), cy(i), cz(i));
+    int mm = g.node(-cx(i), -cy(i), -cz(i));
+    if (kChecked) {
+      mp = in_bounds(w.fault, mp, nodes, kFaultGeometry) ? mp : 0;
+      mm = in_bounds(w.fault, mm, nodes, kFaultGeometry) ? mm : 0;
+    }
     const float2 rp = rs.at(cx(i), cy(i), cz(i));
     const float2 rm = rs.at(-cx(i), -cy(i), -cz(i));
     const float ap = __ldg(&ads[mp]);
@@ -290,10 +305,11 @@ __device__ __forceinline__ void put2(const StepParams &p, const Workspace &w,
     ref = make_float2(__fmul_rn(ws, rd.x), __fmul_rn(ws, rd.y));
   }
   const typename C::T2 e = C::enc_s(o1, o2, ref);
-  if (PARITY == 0)
-    pop_base(f, g, 0, 0, 0)[opp(i) * kTile] = e;
-  else
-    pop_base(f, g, cx(i), cy(i), cz(i))[i * kTile] = e;
+  const int slot = PARITY == 0 ? opp(i) : i;
+  typename C::T2 *dst = f + (PARITY == 0 ? g.pop_off(0, 0, 0) : g.pop_off(cx(i), cy(i), cz(i)));
+  if (!kChecked ||
+      in_bounds(w.fault, (dst - f) + slot * kTile, p.ntiles * kTilePairs, kFaultPopStore))
+    dst[slot * kTile] = e;
 }
 
 // Eq. 1 for both components: (1 - n_s)[f_i - (f_i - f^eq_i)/tau] +
@@ -370,7 +386,7 @@ __device__ __forceinline__ void collide_node(const StepParams &p, const Workspac
   first_moment(f2, j2);
 
   float g1[3], g2[3];
-  force_per_mass<PC>(p, rs, w.ads, w.ads2, g, r1 + r2, g1, g2);
+  force_per_mass<PC>(p, rs, w, g, r1 + r2, g1, g2);
 
   // Eq. 6: common velocity sum_s j_s/tau_s / sum_s rho_s/tau_s, then the
   // Shan-Chen shift tau_s F_tot,s / rho_s = tau_s g_s.
@@ -383,8 +399,10 @@ __device__ __forceinline__ void collide_node(const StepParams &p, const Workspac
     u2[d] = uc + p.tau[1] * g2[d];
   }
 
-  const float ns1 = w.ns[g.node(0, 0, 0)];
-  const float ns2 = PC ? w.ns2[g.node(0, 0, 0)] : ns1;
+  int own = g.node(0, 0, 0);
+  if (!in_bounds(w.fault, own, p.ntiles * kTile, kFaultGeometry)) own = 0;
+  const float ns1 = w.ns[own];
+  const float ns2 = PC ? w.ns2[own] : ns1;
   collide_put2<PARITY, ST>(p, w, g, rs, f1, f2, r1, r2, u1, u2, ns1, ns2);
 }
 
@@ -393,7 +411,7 @@ __device__ __forceinline__ void collide_body(const StepParams &p,
                                              const Workspace &w, bool maybe_res,
                                              int x, int y, int z) {
   const Geo g = make_geo(p, x, y, z);
-  collide_node<PARITY, ST, PC>(p, w, g, GlobalRho{w.rho, g}, maybe_res, x, y, z);
+  collide_node<PARITY, ST, PC>(p, w, g, global_rho(p, w, g), maybe_res, x, y, z);
 }
 
 
@@ -461,7 +479,9 @@ __global__ void __launch_bounds__(DensityShape<CFG>::threads)
   float v1[kQ], v2[kQ];
   load_pops<PARITY, ST>(p, w, g, v1, v2);
   reservoir_state(p, maybe_res, x, y, z, v1, v2);
-  w.rho[g.node(0, 0, 0)] = make_float2(sum19(v1), sum19(v2));
+  const int own = g.node(0, 0, 0);
+  if (in_bounds(w.fault, own, p.ntiles * kTile, kFaultRhoStore))
+    w.rho[own] = make_float2(sum19(v1), sum19(v2));
 }
 
 template <int PARITY, int ST, int CFG, bool PC>
@@ -495,11 +515,14 @@ __global__ void __launch_bounds__(kTile * kFieldsBY * kFieldsBZ)
   first_moment(f2, j2);
   float g1[3], g2[3];
   const float rho = r1 + r2;
-  force_per_mass<PC>(p, GlobalRho{w.rho, g}, w.ads, w.ads2, g, rho, g1, g2);
-  const float fluid = 1.0f - w.ns[g.node(0, 0, 0)];
-  const float fluid2 = PC ? 1.0f - w.ns2[g.node(0, 0, 0)] : fluid;
+  force_per_mass<PC>(p, global_rho(p, w, g), w, g, rho, g1, g2);
+  int own = g.node(0, 0, 0);
+  if (!in_bounds(w.fault, own, p.ntiles * kTile, kFaultGeometry)) own = 0;
+  const float fluid = 1.0f - w.ns[own];
+  const float fluid2 = PC ? 1.0f - w.ns2[own] : fluid;
   const long long L = p.nlin;
   const long long n = x + (long long)p.nx * (y + (long long)p.ny * z);
+  if (!in_bounds(w.fault, n, L, kFaultStage)) return;
   w.stage[n] = r1;
   w.stage[L + n] = r2;
 #pragma unroll
@@ -535,6 +558,7 @@ __global__ void k_init_equilibrium(StepParams p, Workspace w,
   for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
        n += (long long)gridDim.x * blockDim.x) {
     const long long tn = tiled_of_linear(p, n);
+    if (!in_bounds(w.fault, tn, p.ntiles * kTile, kFaultPopStore)) continue;
     typename C::T2 *b = static_cast<typename C::T2 *>(w.f) + (tn / kTile) * kTilePairs + tn % kTile;
     const float r1 = rho1[n], r2 = rho2[n];
     if (storage_local(ST)) w.rho_enc[tn] = make_float2(r1, r2);
@@ -589,8 +613,13 @@ struct RingRho {
   const float2 *row[3];  // ring row of the node's y in planes z - 1, z, z + 1
   int stride;            // one ring row (columns)
   int xm, xc, xp;        // columns of x - 1, x, x + 1 (periodic)
+  const float2 *base;    // the ring and its length (bounds-checked builds)
+  long long size;
+  unsigned *fault;
   __device__ __forceinline__ float2 at(int dx, int dy, int dz) const {
-    return row[dz + 1][dy * stride + (dx < 0 ? xm : (dx > 0 ? xp : xc))];
+    const float2 *q = row[dz + 1] + dy * stride + (dx < 0 ? xm : (dx > 0 ? xp : xc));
+    if (kChecked && !in_bounds(fault, q - base, size, kFaultShared)) q = base;
+    return *q;
   }
   __device__ __forceinline__ float2 late(int dx, int dy, int dz) const {
     return at(dx, dy, dz);
@@ -634,8 +663,12 @@ __global__ void __launch_bounds__(kSpMaxThreads, 2)
       if (y < 0) y += p.ny;
       const Geo g = make_geo(p, x, y, z);
       const float2 rho = node_density<PARITY, ST>(p, w, g, x, y, z);
-      dst[r * ncol + x] = rho;
-      if (own_plane && r >= 1) w.rho[g.node(0, 0, 0)] = rho;
+      if (in_bounds(w.fault, (dst - ring) + r * ncol + x,
+                    (long long)kSpRingPlanes * plane_stride, kFaultShared))
+        dst[r * ncol + x] = rho;
+      const int own = g.node(0, 0, 0);
+      if (own_plane && r >= 1 && in_bounds(w.fault, own, p.ntiles * kTile, kFaultRhoStore))
+        w.rho[own] = rho;
     }
   };
 
@@ -659,6 +692,9 @@ __global__ void __launch_bounds__(kSpMaxThreads, 2)
       rr.xm = xm;
       rr.xc = x;
       rr.xp = xp;
+      rr.base = ring;
+      rr.size = (long long)kSpRingPlanes * plane_stride;
+      rr.fault = w.fault;
       collide_node<PARITY, ST, PC>(p, w, g, rr, p.res.any != 0, x, y, z);
     }
   }
@@ -730,7 +766,9 @@ __global__ void __launch_bounds__(kTile * kBatchBY)
   else
     load_pops<1, ST>(it.p, it.w, g, v1, v2);
   reservoir_state(it.p, maybe_res, x, y, z, v1, v2);
-  it.w.rho[g.node(0, 0, 0)] = make_float2(sum19(v1), sum19(v2));
+  const int own = g.node(0, 0, 0);
+  if (in_bounds(it.w.fault, own, it.p.ntiles * kTile, kFaultRhoStore))
+    it.w.rho[own] = make_float2(sum19(v1), sum19(v2));
 }
 
 // All items of one launch have per-component fractions (PC) or none do.

@@ -196,7 +196,34 @@ struct Workspace {
   float *ads2;       // [ntiles * 32] G_ads,2 * n_s,2, or nullptr
   float *stage;      // [6][nlin] linear (x fastest) staging for host transfers
   double *red;       // [kRedBlocks][kRedK] partial sums + [kRedK] result
+  unsigned *fault;   // bounds-checked builds: bits of the accesses that
+                     // were out of range (FaultBits); unused otherwise
 };
+
+// Bounds-checked builds (compiled with -DHMCSC_CHECKED) test the index of
+// every population, density, geometry, staging and shared-ring access before
+// making it; an index out of range sets a bit in the workspace's fault word
+// and the access is skipped (a load reads element 0 instead).  Default
+// builds compile the tests away.
+enum FaultBits : unsigned {
+  kFaultPopLoad = 1u, kFaultPopStore = 2u, kFaultRhoLoad = 4u,
+  kFaultRhoStore = 8u, kFaultGeometry = 16u, kFaultShared = 32u,
+  kFaultStage = 64u
+};
+#ifdef HMCSC_CHECKED
+constexpr bool kChecked = true;
+__device__ __forceinline__ bool in_bounds(unsigned *fault, long long i, long long n,
+                                          unsigned bit) {
+  if (i >= 0 && i < n) return true;
+  atomicOr(fault, bit);
+  return false;
+}
+#else
+constexpr bool kChecked = false;
+__device__ __forceinline__ bool in_bounds(unsigned *, long long, long long, unsigned) {
+  return true;
+}
+#endif
 
 constexpr int kRedBlocks = 304;  // 2 x 152 SMs
 constexpr int kRedThreads = 256;

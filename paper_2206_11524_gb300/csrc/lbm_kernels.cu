@@ -24,6 +24,7 @@ __global__ void k_geometry(StepParams p, Workspace w,
   for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
        n += (long long)gridDim.x * blockDim.x) {
     const long long tn = tiled_of_linear(p, n);
+    if (!in_bounds(w.fault, tn, p.ntiles * kTile, kFaultGeometry)) continue;
     const float s = ns_lin[n];
     const float g = gads2_lin[n];
     w.ns[tn] = s;
@@ -58,7 +59,7 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce(StepParams p,
     const long long yz = t / p.ntx;
     const int y = (int)(yz % p.ny);
     const int z = (int)(yz / p.ny);
-    const float2 r = w.rho[tn];
+    const float2 r = w.rho[in_bounds(w.fault, tn, p.ntiles * kTile, kFaultRhoLoad) ? tn : 0];
     acc[0] += r.x;
     acc[1] += r.y;
     if (!isfinite(r.x) || !isfinite(r.y)) acc[10] += 1.0;
@@ -130,6 +131,7 @@ size_t workspace_bytes(long long nx, long long ny, long long nz, int storage,
   size_t o_red = take(sizeof(double) * (kRedBlocks + 1) * kRedK);
   size_t o_ns2 = take(per_component ? sizeof(float) * nt : 0);
   size_t o_ads2 = take(per_component ? sizeof(float) * nt : 0);
+  size_t o_fault = take(sizeof(unsigned));
   if (out) {
     out->f = (void *)(base + o_f);
     out->rho = (float2 *)(base + o_rho);
@@ -140,6 +142,7 @@ size_t workspace_bytes(long long nx, long long ny, long long nz, int storage,
     out->red = (double *)(base + o_red);
     out->ns2 = per_component ? (float *)(base + o_ns2) : nullptr;
     out->ads2 = per_component ? (float *)(base + o_ads2) : nullptr;
+    out->fault = (unsigned *)(base + o_fault);
   }
   return off;
 }

@@ -38,6 +38,7 @@ ABI_SYMBOLS = (
     "lbm_batch_step", "lbm_batch_graph_create", "lbm_batch_graph_launch",
     "lbm_batch_graph_destroy", "lbm_set_launch_config",
     "lbm_set_geometry_per_component", "lbm_set_bc_velocity", "lbm_set_single_pass",
+    "lbm_build_checked", "lbm_fault_word",
 )
 LBM_DENSITY_CONFIGS, LBM_COLLIDE_CONFIGS = 3, 4
 SINGLE_PASS_MAX_NX = 256
@@ -97,6 +98,8 @@ def load(path: str | None = None):
         "lbm_set_bc_velocity": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int] + [ctypes.c_double] * 5),
         "lbm_step": (ctypes.c_int, [vp, ctypes.c_int]),
         "lbm_set_single_pass": (ctypes.c_int, [vp, ctypes.c_int]),
+        "lbm_build_checked": (ctypes.c_int, []),
+        "lbm_fault_word": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_uint32), ctypes.c_int]),
         "lbm_density": (ctypes.c_int, [vp]),
         "lbm_collide_stream": (ctypes.c_int, [vp]),
         "lbm_time": (ctypes.c_int64, [vp]),
@@ -206,6 +209,16 @@ def lbm_set_bc_velocity(ctx, face, layers, rho_a, rho_b, ux, uy, uz):
 
 def lbm_step(ctx, n_steps):
     return _check(ctx, load().lbm_step(ctx, int(n_steps)))
+
+
+def lbm_build_checked():
+    return int(load().lbm_build_checked())
+
+
+def lbm_fault_word(ctx, clear=True):
+    v = ctypes.c_uint32(0)
+    _check(ctx, load().lbm_fault_word(ctx, ctypes.byref(v), 1 if clear else 0))
+    return int(v.value)
 
 
 def lbm_set_single_pass(ctx, planes):
