@@ -51,6 +51,7 @@ STORAGE_BYTES = {"f32": (160, 320), "f16": (84, 168), "bf16": (84, 168),
                  "f16l": (92, 176), "bf16l": (92, 176)}
 FALLBACK_HBM_GBS = 6800.0
 NOMINAL_HBM_GBS = 8000.0   # GB300 HBM3e nominal, for context only
+PIPE_FIRST = 4             # first fused-pass launch shape of k_collide_pipe
 
 
 def _peaks():
@@ -392,7 +393,10 @@ def run_gpu(args, world, rank, local):
         step_gbs = bytes_launch / (ms_max / K / 1e3) / 1e9
     else:
         step_gbs = (bytes_density + bytes_collide) * N / (ms_max / K / 1e3) / 1e9
-        kernel_name = "k_collide_stream"
+        # fused-pass shapes from PIPE_FIRST on run the prefetching kernel
+        names = sorted({"k_collide_pipe" if c >= PIPE_FIRST else "k_collide_stream"
+                        for c in (launch or [0, 0, 0])[1:3]})
+        kernel_name = " / ".join(names)
         bytes_launch = bytes_collide * N
         achieved = bytes_collide * N / (ms_collide / 1e3) / 1e9
         traffic_bpn = _profiled_traffic("collide_stream") if storage == "f32" else None

@@ -373,13 +373,13 @@ __device__ __forceinline__ void collide_put2(const StepParams &p, const Workspac
 
 // Moments, forces, equilibrium velocity and collision of node (x, y, z)
 // given its neighbourhood g and the source of the step's densities.
+// collide_loaded starts from the node's 38 populations already decoded (and
+// replaced by the prescribed state inside a reservoir).
 template <int PARITY, int ST, bool PC, typename RS>
-__device__ __forceinline__ void collide_node(const StepParams &p, const Workspace &w,
-                                             const Geo &g, const RS &rs,
-                                             bool maybe_res, int x, int y, int z) {
-  float f1[kQ], f2[kQ];
-  load_pops<PARITY, ST>(p, w, g, f1, f2);
-  reservoir_state(p, maybe_res, x, y, z, f1, f2);
+__device__ __forceinline__ void collide_loaded(const StepParams &p, const Workspace &w,
+                                               const Geo &g, const RS &rs,
+                                               const float (&f1)[kQ],
+                                               const float (&f2)[kQ]) {
   const float r1 = sum19(f1), r2 = sum19(f2);
   float j1[3], j2[3];
   first_moment(f1, j1);
@@ -406,6 +406,16 @@ __device__ __forceinline__ void collide_node(const StepParams &p, const Workspac
   collide_put2<PARITY, ST>(p, w, g, rs, f1, f2, r1, r2, u1, u2, ns1, ns2);
 }
 
+template <int PARITY, int ST, bool PC, typename RS>
+__device__ __forceinline__ void collide_node(const StepParams &p, const Workspace &w,
+                                             const Geo &g, const RS &rs,
+                                             bool maybe_res, int x, int y, int z) {
+  float f1[kQ], f2[kQ];
+  load_pops<PARITY, ST>(p, w, g, f1, f2);
+  reservoir_state(p, maybe_res, x, y, z, f1, f2);
+  collide_loaded<PARITY, ST, PC>(p, w, g, rs, f1, f2);
+}
+
 template <int PARITY, int ST, bool PC>
 __device__ __forceinline__ void collide_body(const StepParams &p,
                                              const Workspace &w, bool maybe_res,
@@ -425,12 +435,31 @@ struct Shape {
 __host__ __device__ constexpr Shape density_shape(int cfg) {
   return cfg == 1 ? Shape{8, 1, 1} : cfg == 2 ? Shape{4, 1, 1} : Shape{4, 2, 1};
 }
+// Shapes of the prefetching fused pass (k_collide_pipe): block 32 x by,
+// blocks per SM, planes per block (zc) and shared-memory buffers (nb, so
+// nb - 1 planes are in flight).
+struct PipeCfg {
+  int by, minb_even, minb_odd, minb_even_local, minb_odd_local, zc, nb;
+};
+// Measured on the 256^3 electrode: one plane in flight (nb = 2) beats two
+// (nb = 3, fewer blocks fit), and the best shapes are 8 rows for even steps
+// and 2 rows at 8 blocks per SM for odd steps.
+__host__ __device__ constexpr PipeCfg pipe_cfg(int cfg) {
+  return cfg == 5   ? PipeCfg{8, 2, 2, 2, 2, 16, 2}
+         : cfg == 6 ? PipeCfg{2, 10, 8, 8, 6, 16, 2}
+                    : PipeCfg{4, 5, 4, 4, 3, 8, 2};
+}
+__host__ __device__ constexpr Shape pipe_shape(int parity, bool local, int cfg) {
+  return Shape{pipe_cfg(cfg).by, 1,
+               parity == 0 ? (local ? pipe_cfg(cfg).minb_even_local : pipe_cfg(cfg).minb_even)
+                           : (local ? pipe_cfg(cfg).minb_odd_local : pipe_cfg(cfg).minb_odd)};
+}
 // The odd step keeps one address per neighbour offset and the *_LOCAL
 // storages also hold the destination densities for encoding: both get more
 // registers per thread (the local odd shape 2 trades occupancy for a budget
 // of 170 registers, which needs no spill).
 __host__ __device__ constexpr Shape collide_shape(int parity, bool local, int cfg) {
-  return parity == 0
+  return cfg >= kCollidePipeFirst ? pipe_shape(parity, local, cfg) : parity == 0
              ? (local ? (cfg == 1 ? Shape{8, 1, 2} : cfg == 2 ? Shape{4, 1, 4}
                          : cfg == 3 ? Shape{2, 4, 2} : Shape{4, 2, 2})
                       : (cfg == 1 ? Shape{8, 1, 3} : cfg == 2 ? Shape{4, 1, 6}
@@ -482,6 +511,94 @@ __global__ void __launch_bounds__(DensityShape<CFG>::threads)
   const int own = g.node(0, 0, 0);
   if (in_bounds(w.fault, own, p.ntiles * kTile, kFaultRhoStore))
     w.rho[own] = make_float2(sum19(v1), sum19(v2));
+}
+
+// ---- fused pass with prefetch ----
+// Shapes kCollidePipeFirst.. of the fused pass: each block owns 32 x by
+// nodes of a run of planes and walks the run plane by plane; every thread
+// copies the populations of its node in the next plane into shared memory
+// (cp.async, two buffers, the thread's own slots only, so no barrier) while
+// it collides the current plane.  The loads of one node overlap the
+// arithmetic of the one before without holding registers; the arithmetic is
+// that of k_collide_stream, so the results are bit-identical.
+template <typename T>
+__device__ __forceinline__ void cp_async(T *smem, const T *gmem) {
+  static_assert(sizeof(T) == 4 || sizeof(T) == 8, "cp.async copies 4 or 8 bytes here");
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(s), "l"(gmem),
+               "n"((int)sizeof(T))
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+
+template <int PARITY, int ST, bool PC, int CFG>
+__global__ void __launch_bounds__(CollideShape<PARITY, ST, CFG>::threads,
+                                  CollideShape<PARITY, ST, CFG>::s.minb)
+    k_collide_pipe(StepParams p, Workspace w) {
+  using C = Codec2<ST>;
+  using T2 = typename C::T2;
+  constexpr Shape S = CollideShape<PARITY, ST, CFG>::s;
+  constexpr int NT = kTile * S.by;
+  constexpr int ZC = pipe_cfg(CFG).zc, NB = pipe_cfg(CFG).nb;
+  extern __shared__ __align__(16) unsigned char pipe_smem[];
+  T2(*buf)[kQ][NT] = reinterpret_cast<T2(*)[kQ][NT]>(pipe_smem);  // [NB][kQ][NT]
+  const int tid = threadIdx.y * kTile + threadIdx.x;
+  const int x = blockIdx.x * kTile + threadIdx.x, y = blockIdx.y * S.by + threadIdx.y;
+  const int z0 = blockIdx.z * ZC, zend = min(z0 + ZC, p.nz);
+  const int xlo = blockIdx.x * kTile, ylo = blockIdx.y * S.by;
+  const bool maybe_res = box_in_reservoir(p, xlo, min(xlo + kTile, p.nx) - 1, ylo,
+                                          min(ylo + S.by, p.ny) - 1, z0, zend - 1);
+  if (x >= p.nx || y >= p.ny || z0 >= zend) return;  // no block-wide sync below
+  const T2 *f = static_cast<const T2 *>(w.f);
+  const long long pairs = p.ntiles * kTilePairs, nodes = p.ntiles * kTile;
+  auto prefetch = [&](int z, int b) {
+    const Geo g = make_geo(p, x, y, z);
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) {
+      const int slot = PARITY == 0 ? i : opp(i);
+      const T2 *src = f + (PARITY == 0 ? g.pop_off(0, 0, 0) : g.pop_off(-cx(i), -cy(i), -cz(i)));
+      if (kChecked && !in_bounds(w.fault, (src - f) + slot * kTile, pairs, kFaultPopLoad))
+        src = f - slot * kTile;
+      cp_async(&buf[b][i][tid], src + slot * kTile);
+    }
+    cp_async_commit();
+  };
+  // NB - 1 planes in flight; one commit group per plane (empty past the end)
+#pragma unroll
+  for (int d = 0; d + 1 < NB; ++d) {
+    if (z0 + d < zend) prefetch(z0 + d, d);
+    else cp_async_commit();
+  }
+  for (int z = z0; z < zend; ++z) {
+    const int b = (z - z0) % NB;
+    const int zp = z + NB - 1;
+    // buffer (zp - z0) % NB was consumed by the previous plane
+    if (zp < zend) prefetch(zp, (zp - z0) % NB);
+    else cp_async_commit();
+    cp_async_wait<NB - 1>();  // the group of plane z is complete
+    const Geo g = make_geo(p, x, y, z);
+    const int own = g.node(0, 0, 0);
+    const float2 own_prev =
+        storage_local(ST)
+            ? __ldg(&w.rho_enc[(kChecked && !in_bounds(w.fault, own, nodes, kFaultRhoLoad)) ? 0 : own])
+            : make_float2(0.f, 0.f);
+    float f1[kQ], f2[kQ];
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) {
+      const float2 v = C::dec(buf[b][i][tid], dec_ref<ST>(p, own_prev, i));
+      f1[i] = v.x;
+      f2[i] = v.y;
+    }
+    reservoir_state(p, maybe_res, x, y, z, f1, f2);
+    collide_loaded<PARITY, ST, PC>(p, w, g, global_rho(p, w, g), f1, f2);
+  }
 }
 
 template <int PARITY, int ST, int CFG, bool PC>

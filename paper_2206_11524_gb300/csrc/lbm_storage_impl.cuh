@@ -34,12 +34,38 @@ void density_any(const StepParams &p, const Workspace &w, int cfg, cudaStream_t 
     default: density_cfg<PARITY, 0>(p, w, s);
   }
 }
+template <int PARITY, bool PC, int CFG>
+void collide_pipe_launch(const StepParams &p, const Workspace &w, cudaStream_t s) {
+  using T2 = typename Codec2<kST>::T2;
+  constexpr Shape S = CollideShape<PARITY, kST, CFG>::s;
+  constexpr PipeCfg P = pipe_cfg(CFG);
+  constexpr int smem = P.nb * kQ * kTile * S.by * (int)sizeof(T2);
+  static bool attr_set = false;
+  if (!attr_set) {
+    if (cudaFuncSetAttribute(k_collide_pipe<PARITY, kST, PC, CFG>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+      return;  // the launch below then reports the error
+    attr_set = true;
+  }
+  const dim3 grid(p.ntx, (p.ny + S.by - 1) / S.by, (p.nz + P.zc - 1) / P.zc);
+  k_collide_pipe<PARITY, kST, PC, CFG><<<grid, dim3(kTile, S.by, 1), smem, s>>>(p, w);
+}
+template <int PARITY, int CFG>
+void collide_pipe_cfg(const StepParams &p, const Workspace &w, cudaStream_t s) {
+  if (w.ns2)
+    collide_pipe_launch<PARITY, true, CFG>(p, w, s);
+  else
+    collide_pipe_launch<PARITY, false, CFG>(p, w, s);
+}
 template <int PARITY>
 void collide_any(const StepParams &p, const Workspace &w, int cfg, cudaStream_t s) {
   switch (cfg) {
     case 1: collide_cfg<PARITY, 1>(p, w, s); break;
     case 2: collide_cfg<PARITY, 2>(p, w, s); break;
     case 3: collide_cfg<PARITY, 3>(p, w, s); break;
+    case 4: collide_pipe_cfg<PARITY, 4>(p, w, s); break;
+    case 5: collide_pipe_cfg<PARITY, 5>(p, w, s); break;
+    case 6: collide_pipe_cfg<PARITY, 6>(p, w, s); break;
     default: collide_cfg<PARITY, 0>(p, w, s);
   }
 }
