@@ -223,13 +223,13 @@ LBM_API const char *lbm_last_error(const lbm_ctx *ctx);
 
 /* Launch shapes of the density pass (0..LBM_DENSITY_CONFIGS-1) and of the
  * fused pass on even and odd steps (0..LBM_COLLIDE_CONFIGS-1): thread-block
- * shape and register budget, 0 = default; fused shapes 4-6 walk runs of
- * planes per block and copy the next plane's populations into shared memory
- * while colliding the current one.  Results do not depend on
+ * shape and register budget, 0 = default; fused shapes 4-7 walk runs of
+ * planes per block and copy the next plane's populations (shape 7: and the
+ * neighbour densities) into shared memory while colliding the current one.  Results do not depend on
  * the choice; speed does (the autotuner measures them per lattice size and
  * storage).  EINVAL if out of range. */
 #define LBM_DENSITY_CONFIGS 3
-#define LBM_COLLIDE_CONFIGS 7
+#define LBM_COLLIDE_CONFIGS 8
 LBM_API lbm_status lbm_set_launch_config(lbm_ctx *ctx, int density_cfg,
                                          int even_cfg, int odd_cfg);
 

@@ -162,10 +162,23 @@ struct GlobalRho {  // the density array written by the density pass
   __device__ __forceinline__ float2 late(int dx, int dy, int dz) const {
     return ld_late(&rho[idx(dx, dy, dz)]);
   }
+  // adhesion sources a_1 = G_ads,2 n_s,1 and a_2 (per-component fractions)
+  const float *__restrict__ ads;
+  const float *__restrict__ ads2;
+  __device__ __forceinline__ int gidx(int dx, int dy, int dz) const {
+    const int n = g.node(dx, dy, dz);
+    return (kChecked && !in_bounds(fault, n, nodes, kFaultGeometry)) ? 0 : n;
+  }
+  __device__ __forceinline__ float a1(int dx, int dy, int dz) const {
+    return __ldg(&ads[gidx(dx, dy, dz)]);
+  }
+  __device__ __forceinline__ float a2(int dx, int dy, int dz) const {
+    return __ldg(&ads2[gidx(dx, dy, dz)]);
+  }
 };
 __device__ __forceinline__ GlobalRho global_rho(const StepParams &p, const Workspace &w,
                                                 const Geo &g) {
-  return GlobalRho{w.rho, g, p.ntiles * kTile, w.fault};
+  return GlobalRho{w.rho, g, p.ntiles * kTile, w.fault, w.ads, w.ads2};
 }
 
 // Total force per unit mass of each component, F_tot,sigma / rho_sigma
@@ -182,28 +195,19 @@ __device__ __forceinline__ void force_per_mass(const StepParams &p, const RS &rs
                                                const Workspace &w, const Geo &g,
                                                float rho_tot, float (&g1)[3],
                                                float (&g2)[3]) {
-  const float *__restrict__ ads = w.ads;
-  const float *__restrict__ ads2 = w.ads2;
-  const long long nodes = p.ntiles * kTile;
   float s1[3] = {0.f, 0.f, 0.f}, s2[3] = {0.f, 0.f, 0.f};
   float sa[3] = {0.f, 0.f, 0.f}, sb[3] = {0.f, 0.f, 0.f};
 #pragma unroll
   for (int i = 1; i <= 9; ++i) {
-    int mp = g.node(cx(i), cy(i), cz(i));
-    int mm = g.node(-cx(i), -cy(i), -cz(i));
-    if (kChecked) {
-      mp = in_bounds(w.fault, mp, nodes, kFaultGeometry) ? mp : 0;
-      mm = in_bounds(w.fault, mm, nodes, kFaultGeometry) ? mm : 0;
-    }
     const float2 rp = rs.at(cx(i), cy(i), cz(i));
     const float2 rm = rs.at(-cx(i), -cy(i), -cz(i));
-    const float ap = __ldg(&ads[mp]);
-    const float am = __ldg(&ads[mm]);
+    const float ap = rs.a1(cx(i), cy(i), cz(i));
+    const float am = rs.a1(-cx(i), -cy(i), -cz(i));
     const float d1 = wgt(i) * (rp.x - rm.x);
     const float d2 = wgt(i) * (rp.y - rm.y);
     const float da = wgt(i) * (ap - am);
     float db = 0.0f;
-    if (PC) db = wgt(i) * (__ldg(&ads2[mp]) - __ldg(&ads2[mm]));
+    if (PC) db = wgt(i) * (rs.a2(cx(i), cy(i), cz(i)) - rs.a2(-cx(i), -cy(i), -cz(i)));
     if (cx(i)) { s1[0] += cx(i) > 0 ? d1 : -d1; s2[0] += cx(i) > 0 ? d2 : -d2; sa[0] += cx(i) > 0 ? da : -da; if (PC) sb[0] += cx(i) > 0 ? db : -db; }
     if (cy(i)) { s1[1] += cy(i) > 0 ? d1 : -d1; s2[1] += cy(i) > 0 ? d2 : -d2; sa[1] += cy(i) > 0 ? da : -da; if (PC) sb[1] += cy(i) > 0 ? db : -db; }
     if (cz(i)) { s1[2] += cz(i) > 0 ? d1 : -d1; s2[2] += cz(i) > 0 ? d2 : -d2; sa[2] += cz(i) > 0 ? da : -da; if (PC) sb[2] += cz(i) > 0 ? db : -db; }
@@ -440,15 +444,51 @@ __host__ __device__ constexpr Shape density_shape(int cfg) {
 // nb - 1 planes are in flight).
 struct PipeCfg {
   int by, minb_even, minb_odd, minb_even_local, minb_odd_local, zc, nb;
+  bool ring;  // neighbour densities and adhesion sources also staged in
+              // shared memory (a five-plane ring filled by the block)
 };
 // Measured on the 256^3 electrode: one plane in flight (nb = 2) beats two
 // (nb = 3, fewer blocks fit), and the best shapes are 8 rows for even steps
-// and 2 rows at 8 blocks per SM for odd steps.
+// and 2 rows at 8 blocks per SM for odd steps.  Staging the neighbour
+// densities in a ring as well (shape 7) helps the half-offset odd step by
+// ~3 % and slows the float32 one (the per-plane barrier).
 __host__ __device__ constexpr PipeCfg pipe_cfg(int cfg) {
-  return cfg == 5   ? PipeCfg{8, 2, 2, 2, 2, 16, 2}
-         : cfg == 6 ? PipeCfg{2, 10, 8, 8, 6, 16, 2}
-                    : PipeCfg{4, 5, 4, 4, 3, 8, 2};
+  return cfg == 5   ? PipeCfg{8, 2, 2, 2, 2, 16, 2, false}
+         : cfg == 6 ? PipeCfg{2, 10, 8, 8, 6, 16, 2, false}
+         : cfg == 7 ? PipeCfg{2, 10, 8, 8, 6, 16, 2, true}
+                    : PipeCfg{4, 5, 4, 4, 3, 8, 2, false};
 }
+// Shared memory of a prefetching block: population buffers, then (ring)
+// five planes of (by + 2) x 34 density pairs and adhesion sources.
+constexpr int kPipeRingPlanes = 5, kPipeRingCols = kTile + 2;
+__host__ __device__ constexpr int pipe_smem_bytes(int cfg, int pair_bytes, bool pc) {
+  return pipe_cfg(cfg).nb * kQ * kTile * pipe_cfg(cfg).by * pair_bytes +
+         (pipe_cfg(cfg).ring ? kPipeRingPlanes * (pipe_cfg(cfg).by + 2) * kPipeRingCols *
+                                   (8 + 4 + (pc ? 4 : 0))
+                             : 0);
+}
+
+// Neighbour densities and adhesion sources from the shared-memory ring of a
+// prefetching block: row pointers of the node's ring row in planes z - 1,
+// z, z + 1 and the node's column.
+struct SmemStencil {
+  const float2 *rho[3];
+  const float *a[3];
+  const float *b[3];
+  int c;
+  __device__ __forceinline__ float2 at(int dx, int dy, int dz) const {
+    return rho[dz + 1][dy * kPipeRingCols + c + dx];
+  }
+  __device__ __forceinline__ float2 late(int dx, int dy, int dz) const {
+    return at(dx, dy, dz);
+  }
+  __device__ __forceinline__ float a1(int dx, int dy, int dz) const {
+    return a[dz + 1][dy * kPipeRingCols + c + dx];
+  }
+  __device__ __forceinline__ float a2(int dx, int dy, int dz) const {
+    return b[dz + 1][dy * kPipeRingCols + c + dx];
+  }
+};
 __host__ __device__ constexpr Shape pipe_shape(int parity, bool local, int cfg) {
   return Shape{pipe_cfg(cfg).by, 1,
                parity == 0 ? (local ? pipe_cfg(cfg).minb_even_local : pipe_cfg(cfg).minb_even)
@@ -546,19 +586,29 @@ __global__ void __launch_bounds__(CollideShape<PARITY, ST, CFG>::threads,
   using T2 = typename C::T2;
   constexpr Shape S = CollideShape<PARITY, ST, CFG>::s;
   constexpr int NT = kTile * S.by;
-  constexpr int ZC = pipe_cfg(CFG).zc, NB = pipe_cfg(CFG).nb;
+  constexpr PipeCfg P = pipe_cfg(CFG);
+  constexpr int ZC = P.zc, NB = P.nb, R = S.by + 2, RC = kPipeRingCols;
   extern __shared__ __align__(16) unsigned char pipe_smem[];
   T2(*buf)[kQ][NT] = reinterpret_cast<T2(*)[kQ][NT]>(pipe_smem);  // [NB][kQ][NT]
+  // ring: [5][R][RC] density pairs, then adhesion sources a_1 (and a_2)
+  float2 *ring_rho = reinterpret_cast<float2 *>(pipe_smem + NB * kQ * NT * sizeof(T2));
+  float *ring_a = reinterpret_cast<float *>(ring_rho + kPipeRingPlanes * R * RC);
+  float *ring_b = ring_a + kPipeRingPlanes * R * RC;
   const int tid = threadIdx.y * kTile + threadIdx.x;
   const int x = blockIdx.x * kTile + threadIdx.x, y = blockIdx.y * S.by + threadIdx.y;
   const int z0 = blockIdx.z * ZC, zend = min(z0 + ZC, p.nz);
   const int xlo = blockIdx.x * kTile, ylo = blockIdx.y * S.by;
   const bool maybe_res = box_in_reservoir(p, xlo, min(xlo + kTile, p.nx) - 1, ylo,
                                           min(ylo + S.by, p.ny) - 1, z0, zend - 1);
-  if (x >= p.nx || y >= p.ny || z0 >= zend) return;  // no block-wide sync below
+  const bool active = x < p.nx && y < p.ny;
+  // Without the ring no thread reads another's shared memory and idle
+  // threads may leave; with it every thread fills the ring and meets the
+  // per-plane barrier.
+  if (z0 >= zend || (!P.ring && !active)) return;
   const T2 *f = static_cast<const T2 *>(w.f);
   const long long pairs = p.ntiles * kTilePairs, nodes = p.ntiles * kTile;
   auto prefetch = [&](int z, int b) {
+    if (!active) return;
     const Geo g = make_geo(p, x, y, z);
 #pragma unroll
     for (int i = 0; i < kQ; ++i) {
@@ -568,21 +618,58 @@ __global__ void __launch_bounds__(CollideShape<PARITY, ST, CFG>::threads,
         src = f - slot * kTile;
       cp_async(&buf[b][i][tid], src + slot * kTile);
     }
-    cp_async_commit();
   };
-  // NB - 1 planes in flight; one commit group per plane (empty past the end)
+  // ring plane of z (z0 - 1 <= z <= zend): rows y0 - 1 .. y0 + by, columns
+  // x0 - 1 .. x0 + 32, periodic
+  auto fill_ring = [&](int z) {
+    const int slot = (z - z0 + 1) % kPipeRingPlanes;
+    const int zw = z < 0 ? z + p.nz : (z >= p.nz ? z - p.nz : z);
+    for (int e = tid; e < R * RC; e += NT) {
+      const int r = e / RC, c = e % RC;
+      int xw = xlo + c - 1, yw = ylo + r - 1;
+      xw = xw < 0 ? xw + p.nx : (xw >= p.nx ? xw % p.nx : xw);
+      yw = yw < 0 ? yw + p.ny : (yw >= p.ny ? yw % p.ny : yw);
+      long long n = ((long long)(zw * p.ny + yw) * p.ntx + xw / kTile) * kTile + xw % kTile;
+      if (kChecked && !in_bounds(w.fault, n, nodes, kFaultRhoLoad)) n = 0;
+      const int k = (slot * R + r) * RC + c;
+      cp_async(&ring_rho[k], &w.rho[n]);
+      cp_async(&ring_a[k], &w.ads[n]);
+      if (PC) cp_async(&ring_b[k], &w.ads2[n]);
+    }
+  };
+  if constexpr (!P.ring) {
+    // NB - 1 planes in flight; one commit group per plane (empty past the end)
 #pragma unroll
-  for (int d = 0; d + 1 < NB; ++d) {
-    if (z0 + d < zend) prefetch(z0 + d, d);
-    else cp_async_commit();
+    for (int d = 0; d + 1 < NB; ++d) {
+      if (z0 + d < zend) prefetch(z0 + d, d);
+      cp_async_commit();
+    }
+  } else {
+    prefetch(z0, 0);
+    fill_ring(z0 - 1);
+    fill_ring(z0);
+    fill_ring(z0 + 1);
+    cp_async_commit();
   }
   for (int z = z0; z < zend; ++z) {
     const int b = (z - z0) % NB;
-    const int zp = z + NB - 1;
-    // buffer (zp - z0) % NB was consumed by the previous plane
-    if (zp < zend) prefetch(zp, (zp - z0) % NB);
-    else cp_async_commit();
-    cp_async_wait<NB - 1>();  // the group of plane z is complete
+    if constexpr (!P.ring) {
+      const int zp = z + NB - 1;
+      // buffer (zp - z0) % NB was consumed by the previous plane
+      if (zp < zend) prefetch(zp, (zp - z0) % NB);
+      cp_async_commit();
+      cp_async_wait<NB - 1>();  // the group of plane z is complete
+    } else {
+      // next plane's populations and the ring plane after it; the ring slot
+      // refilled here was last read two planes ago, before the previous
+      // barrier
+      if (z + 1 < zend) prefetch(z + 1, (z + 1 - z0) % NB);
+      if (z + 2 <= zend) fill_ring(z + 2);
+      cp_async_commit();
+      cp_async_wait<1>();   // this thread's copies for plane z are complete
+      __syncthreads();      // and every thread's ring copies too
+    }
+    if (!active) continue;
     const Geo g = make_geo(p, x, y, z);
     const int own = g.node(0, 0, 0);
     const float2 own_prev =
@@ -597,7 +684,21 @@ __global__ void __launch_bounds__(CollideShape<PARITY, ST, CFG>::threads,
       f2[i] = v.y;
     }
     reservoir_state(p, maybe_res, x, y, z, f1, f2);
-    collide_loaded<PARITY, ST, PC>(p, w, g, global_rho(p, w, g), f1, f2);
+    if constexpr (!P.ring) {
+      collide_loaded<PARITY, ST, PC>(p, w, g, global_rho(p, w, g), f1, f2);
+    } else {
+      SmemStencil st;
+      const int r = threadIdx.y + 1;
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        const int k = (((z - 1 + d) - z0 + 1) % kPipeRingPlanes * R + r) * RC;
+        st.rho[d] = ring_rho + k;
+        st.a[d] = ring_a + k;
+        st.b[d] = ring_b + k;
+      }
+      st.c = threadIdx.x + 1;
+      collide_loaded<PARITY, ST, PC>(p, w, g, st, f1, f2);
+    }
   }
 }
 
@@ -733,6 +834,7 @@ struct RingRho {
   const float2 *base;    // the ring and its length (bounds-checked builds)
   long long size;
   unsigned *fault;
+  const GlobalRho *glob; // adhesion sources come from global memory
   __device__ __forceinline__ float2 at(int dx, int dy, int dz) const {
     const float2 *q = row[dz + 1] + dy * stride + (dx < 0 ? xm : (dx > 0 ? xp : xc));
     if (kChecked && !in_bounds(fault, q - base, size, kFaultShared)) q = base;
@@ -740,6 +842,12 @@ struct RingRho {
   }
   __device__ __forceinline__ float2 late(int dx, int dy, int dz) const {
     return at(dx, dy, dz);
+  }
+  __device__ __forceinline__ float a1(int dx, int dy, int dz) const {
+    return glob->a1(dx, dy, dz);
+  }
+  __device__ __forceinline__ float a2(int dx, int dy, int dz) const {
+    return glob->a2(dx, dy, dz);
   }
 };
 
@@ -812,6 +920,8 @@ __global__ void __launch_bounds__(kSpMaxThreads, 2)
       rr.base = ring;
       rr.size = (long long)kSpRingPlanes * plane_stride;
       rr.fault = w.fault;
+      const GlobalRho glob = global_rho(p, w, g);
+      rr.glob = &glob;
       collide_node<PARITY, ST, PC>(p, w, g, rr, p.res.any != 0, x, y, z);
     }
   }

@@ -39,7 +39,7 @@ void collide_pipe_launch(const StepParams &p, const Workspace &w, cudaStream_t s
   using T2 = typename Codec2<kST>::T2;
   constexpr Shape S = CollideShape<PARITY, kST, CFG>::s;
   constexpr PipeCfg P = pipe_cfg(CFG);
-  constexpr int smem = P.nb * kQ * kTile * S.by * (int)sizeof(T2);
+  constexpr int smem = pipe_smem_bytes(CFG, (int)sizeof(T2), PC);
   static bool attr_set = false;
   if (!attr_set) {
     if (cudaFuncSetAttribute(k_collide_pipe<PARITY, kST, PC, CFG>,
@@ -66,6 +66,7 @@ void collide_any(const StepParams &p, const Workspace &w, int cfg, cudaStream_t 
     case 4: collide_pipe_cfg<PARITY, 4>(p, w, s); break;
     case 5: collide_pipe_cfg<PARITY, 5>(p, w, s); break;
     case 6: collide_pipe_cfg<PARITY, 6>(p, w, s); break;
+    case 7: collide_pipe_cfg<PARITY, 7>(p, w, s); break;
     default: collide_cfg<PARITY, 0>(p, w, s);
   }
 }
