@@ -29,6 +29,13 @@ def test_header_declares_the_binding_symbols():
     assert _header_symbols() == sorted(lbm.ABI_SYMBOLS)
 
 
+def test_header_constants_match_the_binding():
+    src = open(os.path.join(ROOT, "include", "lbm.h")).read()
+    defs = dict(re.findall(r"^#define\s+(LBM_\w+)\s+(\d+)", src, re.M))
+    for name in ("LBM_DENSITY_CONFIGS", "LBM_COLLIDE_CONFIGS", "LBM_BATCH_MAX"):
+        assert int(defs[name]) == getattr(lbm, name), name
+
+
 def test_library_exports_every_declared_symbol(lib):
     for name in _header_symbols():
         assert hasattr(lib, name), name
