@@ -311,6 +311,7 @@ def run_gpu(args, world, rank, local):
         from paper_2206_11524_gb300 import autotune
         table = autotune.TuneTable(os.path.join(tempfile.mkdtemp(), "launch_table.json"))
         launch = list(lat.autotune(table))
+    launch = list(lat.launch_config())   # the shapes actually in use
 
     single = args.single_pass > 0
     if single:
@@ -395,7 +396,7 @@ def run_gpu(args, world, rank, local):
         step_gbs = (bytes_density + bytes_collide) * N / (ms_max / K / 1e3) / 1e9
         # fused-pass shapes from PIPE_FIRST on run the prefetching kernel
         names = sorted({"k_collide_pipe" if c >= PIPE_FIRST else "k_collide_stream"
-                        for c in (launch or [0, 0, 0])[1:3]})
+                        for c in launch[1:3]})
         kernel_name = " / ".join(names)
         bytes_launch = bytes_collide * N
         achieved = bytes_collide * N / (ms_collide / 1e3) / 1e9

@@ -266,7 +266,12 @@ lbm_status lbm_create(const lbm_params *params, void *d_workspace,
   c->have_geometry = false;
   c->have_state = false;
   c->bc_version = 0;
-  c->launch_cfg[0] = c->launch_cfg[1] = c->launch_cfg[2] = 0;
+  // start from the shapes measured fastest for the storage on the 256^3
+  // electrode (the tuner refines them per size)
+  const bool local = hmcsc::storage_local(params->storage);
+  c->launch_cfg[0] = params->storage == LBM_STORAGE_F32 ? 1 : 0;
+  c->launch_cfg[1] = local ? 2 : 5;
+  c->launch_cfg[2] = local ? 2 : (params->storage == LBM_STORAGE_F32 ? 6 : 7);
   c->single_pass_zc = 0;
   // Zero the whole workspace once so padding lanes hold defined values.
   cudaError_t e = cudaMemsetAsync(d_workspace, 0, need, c->stream);
@@ -876,6 +881,15 @@ lbm_status lbm_set_launch_config(lbm_ctx *c, int density_cfg, int even_cfg,
   c->launch_cfg[0] = density_cfg;
   c->launch_cfg[1] = even_cfg;
   c->launch_cfg[2] = odd_cfg;
+  return LBM_OK;
+}
+
+lbm_status lbm_get_launch_config(const lbm_ctx *c, int *density_cfg, int *even_cfg,
+                                 int *odd_cfg) {
+  if (!c || !density_cfg || !even_cfg || !odd_cfg) return LBM_EINVAL;
+  *density_cfg = c->launch_cfg[0];
+  *even_cfg = c->launch_cfg[1];
+  *odd_cfg = c->launch_cfg[2];
   return LBM_OK;
 }
 

@@ -38,7 +38,7 @@ ABI_SYMBOLS = (
     "lbm_batch_step", "lbm_batch_graph_create", "lbm_batch_graph_launch",
     "lbm_batch_graph_destroy", "lbm_set_launch_config",
     "lbm_set_geometry_per_component", "lbm_set_bc_velocity", "lbm_set_single_pass",
-    "lbm_build_checked", "lbm_fault_word",
+    "lbm_build_checked", "lbm_fault_word", "lbm_get_launch_config",
 )
 LBM_DENSITY_CONFIGS, LBM_COLLIDE_CONFIGS = 3, 8
 SINGLE_PASS_MAX_NX = 256
@@ -99,6 +99,7 @@ def load(path: str | None = None):
         "lbm_step": (ctypes.c_int, [vp, ctypes.c_int]),
         "lbm_set_single_pass": (ctypes.c_int, [vp, ctypes.c_int]),
         "lbm_build_checked": (ctypes.c_int, []),
+        "lbm_get_launch_config": (ctypes.c_int, [vp] + [ctypes.POINTER(ctypes.c_int)] * 3),
         "lbm_fault_word": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_uint32), ctypes.c_int]),
         "lbm_density": (ctypes.c_int, [vp]),
         "lbm_collide_stream": (ctypes.c_int, [vp]),
@@ -209,6 +210,12 @@ def lbm_set_bc_velocity(ctx, face, layers, rho_a, rho_b, ux, uy, uz):
 
 def lbm_step(ctx, n_steps):
     return _check(ctx, load().lbm_step(ctx, int(n_steps)))
+
+
+def lbm_get_launch_config(ctx):
+    v = [ctypes.c_int(0) for _ in range(3)]
+    _check(ctx, load().lbm_get_launch_config(ctx, *[ctypes.byref(x) for x in v]))
+    return tuple(x.value for x in v)
 
 
 def lbm_build_checked():
@@ -410,6 +417,10 @@ class Lattice:
 
     def step(self, n=1):
         lbm_step(self.ctx, n)
+
+    def launch_config(self):
+        """(density, even, odd) launch shapes in use."""
+        return lbm_get_launch_config(self.ctx)
 
     def set_single_pass(self, planes):
         """Single-pass lbm_step with boxes of `planes` planes (0: two passes)."""
