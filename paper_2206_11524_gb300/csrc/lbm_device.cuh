@@ -6,12 +6,18 @@
 //   k_collide_stream moments, Shan-Chen forces (Eqs. 3-5), equilibrium
 //                    velocity (Eq. 6), equilibrium (Eq. A.3), gray collision
 //                    with partial bounce-back (Eq. 1) and in-place streaming
+//   (or k_collide_pipe, the same arithmetic with the next plane's
+//   populations copied into shared memory ahead of use)
+// plus, as options, the single-pass sweep (k_sp_bulk + k_sp_seams) and the
+// batched kernels that advance many lattices per launch.
 //
 // Density reservoirs (Sec. 4) reset their layers to the equilibrium at rest
-// after every step.  No kernel writes that reset: every reader of a node's
-// populations (both passes, the fields pass, the host read-back) takes
-// f_i = w_i rho_res for a node inside a reservoir, which is the state the
-// reset defines, and what neighbours streamed into its slots is never read.
+// after every step, velocity boundary cells (Sec. 3.1) to the equilibrium at
+// their velocity.  No kernel writes that reset: every reader of a node's
+// populations (both passes, the fields pass, the host read-back) takes the
+// prescribed equilibrium for a node inside such a layer, which is the state
+// the reset defines, and what neighbours streamed into its slots is never
+// read.
 // StepParams::res holds the reservoirs that were in effect at the end of the
 // previous step.
 //
