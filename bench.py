@@ -73,10 +73,14 @@ def _seam_nodes(nx, ny, nz, planes, box_rows=8):
 
 
 def _kernel_sha():
+    """Hash of the device code (comments and blank lines removed, so that an
+    edit of comments alone keeps a capture valid)."""
+    import re
     h = hashlib.sha256()
     for f in ("lbm_device.cuh", "lbm_internal.cuh", "lbm_storage_impl.cuh"):
-        with open(os.path.join(ROOT, "paper_2206_11524_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_2206_11524_gb300", "csrc", f)) as fh:
+            code = re.sub(r"//[^\n]*", "", fh.read())
+        h.update("\n".join(l.rstrip() for l in code.splitlines() if l.strip()).encode())
     return h.hexdigest()[:16]
 
 
