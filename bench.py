@@ -51,7 +51,7 @@ STORAGE_BYTES = {"f32": (160, 320), "f16": (84, 168), "bf16": (84, 168),
                  "f16l": (92, 176), "bf16l": (92, 176)}
 FALLBACK_HBM_GBS = 6800.0
 NOMINAL_HBM_GBS = 8000.0   # GB300 HBM3e nominal, for context only
-PIPE_FIRST = 4             # first fused-pass launch shape of k_collide_pipe
+PIPE_FIRST = 5             # first fused-pass launch shape of k_collide_pipe
 
 
 def _peaks():

@@ -223,16 +223,17 @@ LBM_API const char *lbm_last_error(const lbm_ctx *ctx);
 
 /* Launch shapes of the density pass (0..LBM_DENSITY_CONFIGS-1) and of the
  * fused pass on even and odd steps (0..LBM_COLLIDE_CONFIGS-1): thread-block
- * shape and register budget; fused shapes 4-7 walk runs of planes per block
- * and copy the next plane's populations (shape 7: and the neighbour
- * densities) into shared memory while colliding the current one.  A new
- * context starts with the shapes measured fastest for its storage on a
- * 256^3 lattice (float32 1/5/6, half and bfloat16 offsets 0/5/7, local
- * offsets 0/2/2).  Results do not depend on the choice; speed does (the
+ * shape and register budget; fused shape 4 stores with the streaming cache
+ * policy; fused shapes 5-9 walk runs of planes per block and copy the next
+ * plane's populations (shapes 8-9: and the neighbour densities) into shared
+ * memory while colliding the current one (shape 9: with streaming stores).
+ * A new context starts with the shapes measured fastest for its storage on
+ * a 256^3 lattice (float32 1/6/7, half and bfloat16 offsets 0/6/8, local
+ * offsets 0/9/9).  Results do not depend on the choice; speed does (the
  * autotuner measures them per lattice size and storage).  EINVAL if out of
  * range. */
 #define LBM_DENSITY_CONFIGS 3
-#define LBM_COLLIDE_CONFIGS 8
+#define LBM_COLLIDE_CONFIGS 10
 LBM_API lbm_status lbm_set_launch_config(lbm_ctx *ctx, int density_cfg,
                                          int even_cfg, int odd_cfg);
 /* The shapes in use (EINVAL if an argument is NULL). */

@@ -57,11 +57,20 @@ class TuneTable:
 
 
 def _scratch(nx, ny, nz, storage):
+    """A lattice shaped like an imbibition run: solid, open and gray nodes
+    mixed, adhesion in the gray ones, density reservoirs on both x faces
+    (the reservoir checks are part of what the shapes pay for)."""
     shape = (nz, ny, nx)
     rng = np.random.default_rng(0)
     lat = lbm.Lattice(nx, ny, nz, tau=(1.0, 1.0), G=1.75, storage=storage,
                       rho0=(0.5, 0.5))
-    lat.set_geometry(np.full(shape, 0.3), np.zeros(shape))
+    u = rng.random(shape)
+    ns = np.where(u < 0.5, 1.0, np.where(u < 0.8, 0.0, 0.2 + 0.7 * rng.random(shape)))
+    lat.set_geometry(ns, np.where((ns > 0) & (ns < 1), 0.2, 0.0))
+    layers = min(4, nx // 2)
+    if layers > 0:
+        lat.set_bc(0, layers, 1.04, 0.01)
+        lat.set_bc(1, layers, 0.01, 0.99)
     ra = np.where(rng.random(shape) < 0.5, 0.99, 0.03)
     lat.init_equilibrium(ra, 1.02 - ra)
     return lat

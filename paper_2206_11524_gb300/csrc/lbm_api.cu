@@ -269,9 +269,10 @@ lbm_status lbm_create(const lbm_params *params, void *d_workspace,
   // start from the shapes measured fastest for the storage on the 256^3
   // electrode (the tuner refines them per size)
   const bool local = hmcsc::storage_local(params->storage);
-  c->launch_cfg[0] = params->storage == LBM_STORAGE_F32 ? 1 : 0;
-  c->launch_cfg[1] = local ? 2 : 5;
-  c->launch_cfg[2] = local ? 2 : (params->storage == LBM_STORAGE_F32 ? 6 : 7);
+  const bool f32 = params->storage == LBM_STORAGE_F32;
+  c->launch_cfg[0] = f32 ? 1 : 0;
+  c->launch_cfg[1] = local ? 9 : 6;
+  c->launch_cfg[2] = local ? 9 : (f32 ? 7 : 8);
   c->single_pass_zc = 0;
   // Zero the whole workspace once so padding lanes hold defined values.
   cudaError_t e = cudaMemsetAsync(d_workspace, 0, need, c->stream);

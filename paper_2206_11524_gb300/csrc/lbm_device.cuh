@@ -301,7 +301,7 @@ __device__ __forceinline__ void reservoir_state(const StepParams &p, bool maybe,
 // reference: w_i times the destination's density at this step (*_LOCAL;
 // rho_s for the rest population, the density pass's value otherwise), or the
 // constants w_i rho0_sigma (*_OFFSET).
-template <int PARITY, int ST, typename RS>
+template <int PARITY, int ST, typename RS, bool CS = false>
 __device__ __forceinline__ void put2(const StepParams &p, const Workspace &w,
                                      const Geo &g, const RS &rs, int i, float o1,
                                      float o2, float r1, float r2) {
@@ -319,7 +319,12 @@ __device__ __forceinline__ void put2(const StepParams &p, const Workspace &w,
   typename C::T2 *dst = f + (PARITY == 0 ? g.pop_off(0, 0, 0) : g.pop_off(cx(i), cy(i), cz(i)));
   if (!kChecked ||
       in_bounds(w.fault, (dst - f) + slot * kTile, p.ntiles * kTilePairs, kFaultPopStore))
-    dst[slot * kTile] = e;
+  {
+    if (CS)
+      __stcs(&dst[slot * kTile], e);  // streaming: evict first from the caches
+    else
+      dst[slot * kTile] = e;
+  }
 }
 
 // Eq. 1 for both components: (1 - n_s)[f_i - (f_i - f^eq_i)/tau] +
@@ -361,7 +366,7 @@ struct Relax {
   }
 };
 
-template <int PARITY, int ST, typename RS>
+template <int PARITY, int ST, typename RS, bool CS = false>
 __device__ __forceinline__ void collide_put2(const StepParams &p, const Workspace &w,
                                              const Geo &g, const RS &rs,
                                              const float (&v1)[kQ],
@@ -375,17 +380,17 @@ __device__ __forceinline__ void collide_put2(const StepParams &p, const Workspac
     float o1i, o1j, o2i, o2j;
     c1.pair(i, u1, v1, o1i, o1j);
     c2.pair(i, u2, v2, o2i, o2j);
-    put2<PARITY, ST>(p, w, g, rs, i, o1i, o2i, r1, r2);
-    put2<PARITY, ST>(p, w, g, rs, i + 9, o1j, o2j, r1, r2);
+    put2<PARITY, ST, RS, CS>(p, w, g, rs, i, o1i, o2i, r1, r2);
+    put2<PARITY, ST, RS, CS>(p, w, g, rs, i + 9, o1j, o2j, r1, r2);
   }
-  put2<PARITY, ST>(p, w, g, rs, 0, c1.rest(v1), c2.rest(v2), r1, r2);
+  put2<PARITY, ST, RS, CS>(p, w, g, rs, 0, c1.rest(v1), c2.rest(v2), r1, r2);
 }
 
 // Moments, forces, equilibrium velocity and collision of node (x, y, z)
 // given its neighbourhood g and the source of the step's densities.
 // collide_loaded starts from the node's 38 populations already decoded (and
 // replaced by the prescribed state inside a reservoir).
-template <int PARITY, int ST, bool PC, typename RS>
+template <int PARITY, int ST, bool PC, typename RS, bool CS = false>
 __device__ __forceinline__ void collide_loaded(const StepParams &p, const Workspace &w,
                                                const Geo &g, const RS &rs,
                                                const float (&f1)[kQ],
@@ -413,7 +418,7 @@ __device__ __forceinline__ void collide_loaded(const StepParams &p, const Worksp
   if (!in_bounds(w.fault, own, p.ntiles * kTile, kFaultGeometry)) own = 0;
   const float ns1 = w.ns[own];
   const float ns2 = PC ? w.ns2[own] : ns1;
-  collide_put2<PARITY, ST>(p, w, g, rs, f1, f2, r1, r2, u1, u2, ns1, ns2);
+  collide_put2<PARITY, ST, RS, CS>(p, w, g, rs, f1, f2, r1, r2, u1, u2, ns1, ns2);
 }
 
 template <int PARITY, int ST, bool PC, typename RS>
@@ -426,12 +431,15 @@ __device__ __forceinline__ void collide_node(const StepParams &p, const Workspac
   collide_loaded<PARITY, ST, PC>(p, w, g, rs, f1, f2);
 }
 
-template <int PARITY, int ST, bool PC>
+template <int PARITY, int ST, bool PC, bool CS = false>
 __device__ __forceinline__ void collide_body(const StepParams &p,
                                              const Workspace &w, bool maybe_res,
                                              int x, int y, int z) {
   const Geo g = make_geo(p, x, y, z);
-  collide_node<PARITY, ST, PC>(p, w, g, global_rho(p, w, g), maybe_res, x, y, z);
+  float f1[kQ], f2[kQ];
+  load_pops<PARITY, ST>(p, w, g, f1, f2);
+  reservoir_state(p, maybe_res, x, y, z, f1, f2);
+  collide_loaded<PARITY, ST, PC, GlobalRho, CS>(p, w, g, global_rho(p, w, g), f1, f2);
 }
 
 
@@ -441,6 +449,7 @@ __device__ __forceinline__ void collide_body(const StepParams &p,
 // others per lattice size and storage.
 struct Shape {
   int by, bz, minb;
+  bool cs = false;  // populations stored with the streaming (evict-first) policy
 };
 __host__ __device__ constexpr Shape density_shape(int cfg) {
   return cfg == 1 ? Shape{8, 1, 1} : cfg == 2 ? Shape{4, 1, 1} : Shape{4, 2, 1};
@@ -452,17 +461,21 @@ struct PipeCfg {
   int by, minb_even, minb_odd, minb_even_local, minb_odd_local, zc, nb;
   bool ring;  // neighbour densities and adhesion sources also staged in
               // shared memory (a five-plane ring filled by the block)
+  bool cs;    // streaming stores
 };
 // Measured on the 256^3 electrode: one plane in flight (nb = 2) beats two
 // (nb = 3, fewer blocks fit), and the best shapes are 8 rows for even steps
 // and 2 rows at 8 blocks per SM for odd steps.  Staging the neighbour
-// densities in a ring as well (shape 7) helps the half-offset odd step by
-// ~3 % and slows the float32 one (the per-plane barrier).
+// densities in a ring as well (shape 8) helps the half-offset odd step by
+// ~3 % and the local 16-bit even step by 6 %, and slows the float32 one (the
+// per-plane barrier); with streaming stores (shape 9) the local odd step
+// drops from 0.93 to 0.80 ms.
 __host__ __device__ constexpr PipeCfg pipe_cfg(int cfg) {
-  return cfg == 5   ? PipeCfg{8, 2, 2, 2, 2, 16, 2, false}
-         : cfg == 6 ? PipeCfg{2, 10, 8, 8, 6, 16, 2, false}
-         : cfg == 7 ? PipeCfg{2, 10, 8, 8, 6, 16, 2, true}
-                    : PipeCfg{4, 5, 4, 4, 3, 8, 2, false};
+  return cfg == 6   ? PipeCfg{8, 2, 2, 2, 2, 16, 2, false, false}
+         : cfg == 7 ? PipeCfg{2, 10, 8, 8, 6, 16, 2, false, false}
+         : cfg == 8 ? PipeCfg{2, 10, 8, 8, 6, 16, 2, true, false}
+         : cfg == 9 ? PipeCfg{2, 10, 8, 8, 6, 16, 2, true, true}
+                    : PipeCfg{4, 5, 4, 4, 3, 8, 2, false, false};
 }
 // Shared memory of a prefetching block: population buffers, then (ring)
 // five planes of (by + 2) x 34 density pairs and adhesion sources.
@@ -498,14 +511,18 @@ struct SmemStencil {
 __host__ __device__ constexpr Shape pipe_shape(int parity, bool local, int cfg) {
   return Shape{pipe_cfg(cfg).by, 1,
                parity == 0 ? (local ? pipe_cfg(cfg).minb_even_local : pipe_cfg(cfg).minb_even)
-                           : (local ? pipe_cfg(cfg).minb_odd_local : pipe_cfg(cfg).minb_odd)};
+                           : (local ? pipe_cfg(cfg).minb_odd_local : pipe_cfg(cfg).minb_odd),
+               pipe_cfg(cfg).cs};
 }
 // The odd step keeps one address per neighbour offset and the *_LOCAL
 // storages also hold the destination densities for encoding: both get more
 // registers per thread (the local odd shape 2 trades occupancy for a budget
-// of 170 registers, which needs no spill).
+// of 170 registers, which needs no spill).  Shape 4 stores with the
+// streaming policy (float32 odd step 1.05 -> 0.95 ms in the plain kernel).
 __host__ __device__ constexpr Shape collide_shape(int parity, bool local, int cfg) {
-  return cfg >= kCollidePipeFirst ? pipe_shape(parity, local, cfg) : parity == 0
+  return cfg >= kCollidePipeFirst ? pipe_shape(parity, local, cfg)
+         : cfg == 4 ? (local ? Shape{4, 1, 3, true} : Shape{4, 2, 2, true})
+         : parity == 0
              ? (local ? (cfg == 1 ? Shape{8, 1, 2} : cfg == 2 ? Shape{4, 1, 4}
                          : cfg == 3 ? Shape{2, 4, 2} : Shape{4, 2, 2})
                       : (cfg == 1 ? Shape{8, 1, 3} : cfg == 2 ? Shape{4, 1, 6}
@@ -691,7 +708,7 @@ __global__ void __launch_bounds__(CollideShape<PARITY, ST, CFG>::threads,
     }
     reservoir_state(p, maybe_res, x, y, z, f1, f2);
     if constexpr (!P.ring) {
-      collide_loaded<PARITY, ST, PC>(p, w, g, global_rho(p, w, g), f1, f2);
+      collide_loaded<PARITY, ST, PC, GlobalRho, S.cs>(p, w, g, global_rho(p, w, g), f1, f2);
     } else {
       SmemStencil st;
       const int r = threadIdx.y + 1;
@@ -703,7 +720,7 @@ __global__ void __launch_bounds__(CollideShape<PARITY, ST, CFG>::threads,
         st.b[d] = ring_b + k;
       }
       st.c = threadIdx.x + 1;
-      collide_loaded<PARITY, ST, PC>(p, w, g, st, f1, f2);
+      collide_loaded<PARITY, ST, PC, SmemStencil, S.cs>(p, w, g, st, f1, f2);
     }
   }
 }
@@ -717,7 +734,7 @@ __global__ void __launch_bounds__(CollideShape<PARITY, ST, CFG>::threads,
   block_coords<S.by, S.bz>(x, y, z);
   const bool maybe_res = block_in_reservoir<S.by, S.bz>(p);
   if (x >= p.nx || y >= p.ny || z >= p.nz) return;
-  collide_body<PARITY, ST, PC>(p, w, maybe_res, x, y, z);
+  collide_body<PARITY, ST, PC, S.cs>(p, w, maybe_res, x, y, z);
 }
 
 // Macroscopic fields of the current state into the linear staging planes:

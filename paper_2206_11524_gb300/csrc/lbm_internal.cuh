@@ -300,7 +300,7 @@ cudaError_t launch_geometry(const StepParams &p, const Workspace &w,
 // density_shape / collide_shape in lbm_device.cuh).
 // Fused-pass shapes kCollidePipeFirst and up prefetch the next plane's
 // populations into shared memory (k_collide_pipe, pipe_cfg).
-constexpr int kDensityConfigs = 3, kCollideConfigs = 8, kCollidePipeFirst = 4;
+constexpr int kDensityConfigs = 3, kCollideConfigs = 10, kCollidePipeFirst = 5;
 cudaError_t launch_density(const StepParams &p, const Workspace &w, int parity,
                            int cfg, cudaStream_t s);
 cudaError_t launch_collide_stream(const StepParams &p, const Workspace &w,

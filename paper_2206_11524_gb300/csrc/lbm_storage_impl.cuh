@@ -63,10 +63,12 @@ void collide_any(const StepParams &p, const Workspace &w, int cfg, cudaStream_t 
     case 1: collide_cfg<PARITY, 1>(p, w, s); break;
     case 2: collide_cfg<PARITY, 2>(p, w, s); break;
     case 3: collide_cfg<PARITY, 3>(p, w, s); break;
-    case 4: collide_pipe_cfg<PARITY, 4>(p, w, s); break;
+    case 4: collide_cfg<PARITY, 4>(p, w, s); break;
     case 5: collide_pipe_cfg<PARITY, 5>(p, w, s); break;
     case 6: collide_pipe_cfg<PARITY, 6>(p, w, s); break;
     case 7: collide_pipe_cfg<PARITY, 7>(p, w, s); break;
+    case 8: collide_pipe_cfg<PARITY, 8>(p, w, s); break;
+    case 9: collide_pipe_cfg<PARITY, 9>(p, w, s); break;
     default: collide_cfg<PARITY, 0>(p, w, s);
   }
 }

@@ -40,7 +40,7 @@ ABI_SYMBOLS = (
     "lbm_set_geometry_per_component", "lbm_set_bc_velocity", "lbm_set_single_pass",
     "lbm_build_checked", "lbm_fault_word", "lbm_get_launch_config",
 )
-LBM_DENSITY_CONFIGS, LBM_COLLIDE_CONFIGS = 3, 8
+LBM_DENSITY_CONFIGS, LBM_COLLIDE_CONFIGS = 3, 10
 SINGLE_PASS_MAX_NX = 256
 LBM_BATCH_MAX = 64
 

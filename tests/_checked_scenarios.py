@@ -48,7 +48,7 @@ def run():
     g = _lattice((4, 6, 40), per_component=True, seed=11)
     g.step(3)
     keep("pc", g)
-    for cfg in ((0, 7, 7), (0, 5, 6)):   # prefetching shapes, per component
+    for cfg in ((0, 8, 9), (0, 6, 7)):   # prefetching shapes, per component
         g = _lattice((5, 9, 37), "f32", per_component=True, seed=14)
         g.set_launch_config(*cfg)
         g.step(4)
@@ -57,7 +57,7 @@ def run():
     g.set_single_pass(3)
     g.step(4)
     keep("single", g)
-    for cfg in ((2, 3, 3), (1, 1, 1), (0, 2, 2), (0, 5, 6), (0, 7, 7), (0, 4, 4)):
+    for cfg in ((2, 3, 3), (1, 1, 1), (0, 2, 2), (0, 6, 7), (0, 8, 9), (0, 5, 5), (0, 4, 4)):
         g = _lattice((5, 9, 40), "f16l", seed=13)
         g.set_launch_config(*cfg)
         g.step(2)
