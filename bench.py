@@ -320,8 +320,14 @@ def run_gpu(args, world, rank, local):
     single = args.single_pass > 0
     if single:
         lat.set_single_pass(args.single_pass)
+    wave = None
+    if args.wavefront:
+        wave = [int(v) for v in args.wavefront.split(",")] + [0]
+        wave = wave[:2]
+        lat.set_wavefront(*wave)
+    one_launch = single or wave is not None
     for _ in range(args.warmup):
-        if single:
+        if one_launch:
             lbm.lbm_step(ctx, 1)
         else:
             lbm.lbm_density(ctx)
@@ -342,12 +348,12 @@ def run_gpu(args, world, rank, local):
     for k in range(K):
         e0, e1, e2 = ev[k]
         e0.record(stream)
-        if single:
-            lbm.lbm_step(ctx, 1)   # bulk sweep + seam launches
+        if one_launch:
+            lbm.lbm_step(ctx, 1)   # wavefront launch, or bulk sweep + seam launches
         else:
             lbm.lbm_density(ctx)
         e1.record(stream)
-        if not single:
+        if not one_launch:
             lbm.lbm_collide_stream(ctx)
         e2.record(stream)
     stop.record(stream)
@@ -387,7 +393,15 @@ def run_gpu(args, world, rank, local):
 
     peak, peak_kind = _peaks()
     dims = f"{nx}^3" if nx == ny == nz else f"{nx}x{ny}x{nz}"
-    if single:
+    if wave is not None:
+        # whole step in one launch: the fused pass's bytes (the populations
+        # through DRAM once; the densities written instead of read)
+        kernel_name = "k_wave"
+        bytes_launch = bytes_collide * N
+        achieved = bytes_launch / (ms_density / 1e3) / 1e9
+        traffic_bpn = _profiled_traffic("wave") if storage == "f32" else None
+        step_gbs = bytes_launch / (ms_max / K / 1e3) / 1e9
+    elif single:
         # whole single-pass step: every node 320 B as in the fused pass, and
         # the density pass's 160 B again only for the seam nodes
         n_seam = _seam_nodes(nx, ny, nz, args.single_pass)
@@ -432,14 +446,17 @@ def run_gpu(args, world, rank, local):
                    "l2": "inputs larger than L2 (working set "
                          f"{lat.workspace.numel() / 1e9:.2f} GB)",
                    "parallelism": f"replicas x{world}",
-                   "launch_config": launch},
+                   "launch_config": launch,
+                   "wavefront": ({"shape": wave[0], "lag": wave[1] or 4}
+                                 if wave is not None else None)},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak,
                      "peak_kind": f"{peak_kind} hbm_gbs",
                      "kernel": kernel_name,
                      "algorithmic_bytes_per_node": bytes_launch / N,
                      "traffic": (traffic_bpn * N if traffic_bpn else None)},
-        "kernels_ms": ({"single_pass_step": ms_density} if single else
+        "kernels_ms": ({"wavefront_step": ms_density} if wave is not None else
+                       {"single_pass_step": ms_density} if single else
                        {"density": ms_density, "collide_stream": ms_collide}),
         "step_hbm_gbs": step_gbs,
         "step_frac": step_gbs / peak,
@@ -447,8 +464,9 @@ def run_gpu(args, world, rank, local):
                                  "step": step_gbs / NOMINAL_HBM_GBS},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d / K,
                 "d2h_bytes_per_step": d2h / K},
-        # density pass + fused pass per step, or bulk sweep + 2 seam launches
-        "gpu_launches": (3 if single else 2) * K,
+        # density pass + fused pass per step, bulk sweep + 2 seam launches,
+        # or one wavefront launch
+        "gpu_launches": (1 if wave is not None else 3 if single else 2) * K,
         "clocks": clk,
         "cpu_baseline": cpu,
         "serving": serving,
@@ -473,6 +491,8 @@ def main(argv=None):
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--wavefront", default="",
+                    help="time the wavefront step: SHAPE[,LAG] (see lbm_set_wavefront)")
     ap.add_argument("--single-pass", type=int, default=0,
                     help="time the single-pass step with boxes of about this many planes")
     ap.add_argument("--launch-config", default="",

@@ -169,7 +169,8 @@ LBM_API lbm_status lbm_set_bc_velocity(lbm_ctx *ctx, int face, int layers,
 /* Advance n_steps time steps (Eq. 1 plus the reservoirs), asynchronously on
  * the context's stream.  Each step launches the density pass and the fused
  * force/collide/bounce-back/stream pass, or the single-pass sweep when
- * lbm_set_single_pass enabled it.  n_steps = 0 is a no-op. */
+ * lbm_set_single_pass enabled it, or the wavefront launch when
+ * lbm_set_wavefront enabled it.  n_steps = 0 is a no-op. */
 LBM_API lbm_status lbm_step(lbm_ctx *ctx, int n_steps);
 
 /* Single-pass stepping for lbm_step (planes > 0; 0 = two passes, the
@@ -182,6 +183,25 @@ LBM_API lbm_status lbm_step(lbm_ctx *ctx, int n_steps);
  * to the two-pass step.  Needs nx <= 256 (EINVAL otherwise).  lbm_density /
  * lbm_collide_stream and the batched entry points keep the two passes. */
 LBM_API lbm_status lbm_set_single_pass(lbm_ctx *ctx, int planes);
+
+/* Wavefront stepping for lbm_step (shape > 0; 0 = two passes, the default;
+ * it takes precedence over lbm_set_single_pass): each step is one persistent
+ * cooperative launch over work items, a tile of 32 x by nodes of one plane
+ * each (shape 1: by = 4, 2: by = 2, 3: by = 8), taken in plane order from an
+ * atomic ticket.  An item sums the populations of one plane's tile into the
+ * density array and collides and streams the tile `lag` planes behind it
+ * once the densities that collision reads are published (flags in the
+ * workspace), so the second read of each plane's populations comes from L2
+ * instead of DRAM.  lag = 0 takes the default (4); other values must be
+ * >= 3 (EINVAL otherwise); shapes outside 0..3 are EINVAL.  Results are
+ * bit-identical to the two-pass step.  Every wait in the launch is bounded:
+ * a wait that runs out (which a correct launch never does) leaves that
+ * step's result undefined and sets bit 128 (LBM_FAULT_WAIT) of the word
+ * lbm_fault_word reads, in every build.  lbm_density / lbm_collide_stream
+ * and the batched entry points keep the two passes. */
+#define LBM_WAVE_SHAPES 4
+#define LBM_FAULT_WAIT 128u
+LBM_API lbm_status lbm_set_wavefront(lbm_ctx *ctx, int shape, int lag);
 
 /* The two halves of one step, for callers that time or interleave them:
  * lbm_density (rho_sigma of Eq. A.4 at every node) followed by
@@ -273,11 +293,12 @@ LBM_API void lbm_batch_graph_destroy(lbm_graph *graph);
  * every population, density, geometry, staging and shared-memory index is
  * then tested before the access, and an index out of range sets a bit in a
  * fault word kept in the workspace (1 population load, 2 population store,
- * 4 density load, 8 density store, 16 geometry, 32 shared ring, 64 staging)
- * instead of being used.  lbm_build_checked() returns 1 in such a build, 0
- * otherwise.  lbm_fault_word copies the word to *out after waiting for the
- * context's stream, and zeroes it when clear != 0; in a default build it
- * stays 0.  Errors: EINVAL (NULL), ECUDA. */
+ * 4 density load, 8 density store, 16 geometry, 32 shared ring, 64 staging,
+ * 256 wavefront flag) instead of being used.  lbm_build_checked() returns 1
+ * in such a build, 0 otherwise.  lbm_fault_word copies the word to *out
+ * after waiting for the context's stream, and zeroes it when clear != 0; in
+ * a default build only LBM_FAULT_WAIT (a wavefront wait that ran out) can
+ * set it.  Errors: EINVAL (NULL), ECUDA. */
 LBM_API int lbm_build_checked(void);
 LBM_API lbm_status lbm_fault_word(lbm_ctx *ctx, uint32_t *out, int clear);
 

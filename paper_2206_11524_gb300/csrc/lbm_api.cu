@@ -21,6 +21,8 @@ using hmcsc::kRedBlocks;
 using hmcsc::kRedK;
 
 static_assert(LBM_BATCH_MAX == hmcsc::kBatchMax, "batch limit of the ABI");
+static_assert(LBM_WAVE_SHAPES == hmcsc::kWaveConfigs, "wavefront shapes of the ABI");
+static_assert(LBM_FAULT_WAIT == hmcsc::kFaultWait, "fault bit of the ABI");
 
 struct lbm_ctx {
   lbm_params params;
@@ -38,6 +40,8 @@ struct lbm_ctx {
   uint64_t bc_version;    // bumped by every lbm_set_bc
   int launch_cfg[3];      // launch shapes: density, even fused, odd fused
   int single_pass_zc;     // > 0: lbm_step sweeps once, boxes of this many planes
+  int wave_cfg;           // > 0: lbm_step is one wavefront launch of this shape
+  int wave_lag;           // planes between a plane's density and its collision
   std::string err;
 };
 
@@ -274,6 +278,8 @@ lbm_status lbm_create(const lbm_params *params, void *d_workspace,
   c->launch_cfg[1] = local ? 9 : 6;
   c->launch_cfg[2] = local ? 9 : (f32 ? 7 : 8);
   c->single_pass_zc = 0;
+  c->wave_cfg = 0;
+  c->wave_lag = hmcsc::kWaveLagDefault;
   // Zero the whole workspace once so padding lanes hold defined values.
   cudaError_t e = cudaMemsetAsync(d_workspace, 0, need, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
@@ -533,6 +539,14 @@ lbm_status lbm_step(lbm_ctx *c, int n_steps) {
   if (!c->have_geometry || !c->have_state)
     return fail(c, LBM_ESTATE, "set geometry and state before stepping");
   for (int k = 0; k < n_steps; ++k) {
+    if (c->wave_cfg > 0) {
+      cudaError_t e = hmcsc::launch_wave(c->sp, c->ws, parity(c), c->wave_cfg, c->wave_lag,
+                                         c->stream);
+      if (e != cudaSuccess) return cuda_fail(c, e, "wavefront kernel");
+      c->rho_at = c->t;
+      finish_step(c);
+      continue;
+    }
     if (c->single_pass_zc > 0) {
       // runs of about single_pass_zc planes along z
       const int nz = c->params.nz;
@@ -558,6 +572,20 @@ lbm_status lbm_set_single_pass(lbm_ctx *c, int planes) {
   if (planes > 0 && c->params.nx > hmcsc::kSinglePassMaxNx)
     return fail(c, LBM_EINVAL, "the single-pass step needs nx <= %d", hmcsc::kSinglePassMaxNx);
   c->single_pass_zc = planes;
+  return LBM_OK;
+}
+
+lbm_status lbm_set_wavefront(lbm_ctx *c, int shape, int lag) {
+  if (!c) return LBM_EINVAL;
+  if (shape < 0 || shape >= hmcsc::kWaveConfigs)
+    return fail(c, LBM_EINVAL, "wavefront shape must be in 0..%d", hmcsc::kWaveConfigs - 1);
+  if (lag == 0) lag = hmcsc::kWaveLagDefault;
+  if (lag < hmcsc::kWaveLagMin)
+    return fail(c, LBM_EINVAL, "wavefront lag must be >= %d", hmcsc::kWaveLagMin);
+  if ((long long)(c->params.nz + lag) * c->sp.ntx * c->params.ny > 4294967295LL)
+    return fail(c, LBM_EINVAL, "wavefront lag too large for this lattice");
+  c->wave_cfg = shape;
+  c->wave_lag = lag;
   return LBM_OK;
 }
 

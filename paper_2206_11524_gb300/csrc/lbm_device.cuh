@@ -812,6 +812,192 @@ __global__ void k_init_equilibrium(StepParams p, Workspace w,
   }
 }
 
+// ---- wavefront step: both passes in one persistent launch ----
+// The lattice is cut into items: tile T (32 x by nodes of one plane) of
+// group g, g = 0 .. nz + lag - 1, numbered group-major and taken by the
+// blocks in the order of an atomic ticket.  Item (g, T)
+//   - copies the populations of plane q = g - lag of T (if q >= 0) and of
+//     plane d(g) = (g - 1) mod nz of T (if g < nz) into shared memory,
+//   - waits until the densities of planes q - 1 .. q + 1 of T and of its
+//     eight in-plane neighbour tiles are published, then collides and
+//     streams plane q of T exactly as k_collide_stream does,
+//   - sums the populations of plane d(g) into the density array and
+//     publishes them: the flag of (d(g), T) is set to the launch's epoch.
+// The densities a collision of plane q needs come from groups q .. q + 2,
+// all before g when lag >= 3, so an item waits only on items with smaller
+// tickets; those are held by blocks that are already running, so the launch
+// cannot deadlock for any number of resident blocks (every wait is bounded
+// all the same).  The populations of plane q were read from DRAM by the
+// density part lag - 1 groups earlier (a group is one plane of the lattice,
+// 10 MB at 256^2 in float32) and the collision finds them in L2: one step
+// moves its populations through DRAM once instead of twice.  In-place AA
+// streaming stays race-free: the collision of node n touches only the slots
+// holding n's own populations, whose density part has finished reading
+// them before n's flag is set.
+struct WaveCfg {
+  int by, minb, minb_local;
+};
+__host__ __device__ constexpr WaveCfg wave_cfg(int cfg) {
+  return cfg == 2 ? WaveCfg{2, 8, 6} : cfg == 3 ? WaveCfg{8, 2, 2} : WaveCfg{4, 4, 3};
+}
+template <int ST, int CFG>
+struct WaveShape {
+  static constexpr WaveCfg c = wave_cfg(CFG);
+  static constexpr int threads = kTile * c.by;
+  static constexpr int minb = storage_local(ST) ? c.minb_local : c.minb;
+};
+struct WaveArgs {
+  unsigned items;  // (nz + lag) * tp
+  int tp;          // tiles per plane: ntx * ceil(ny / by)
+  int lag;
+};
+// Polls of one flag before a wait gives up (about a second with the
+// back-off); the item then goes on and the fault word records kFaultWait.
+constexpr unsigned kWaveSpinLimit = 1u << 22;
+
+__device__ __forceinline__ unsigned ld_relaxed(const unsigned *ptr) {
+  unsigned v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(ptr) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(unsigned *ptr, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(ptr), "r"(v) : "memory");
+}
+
+// Densities written earlier in the same launch by other blocks: coherent
+// loads (the flag's acquire orders them), cached in L1 for the stencil.
+struct WaveRho : GlobalRho {
+  __device__ __forceinline__ float2 at(int dx, int dy, int dz) const {
+    return __ldca(&rho[idx(dx, dy, dz)]);
+  }
+  __device__ __forceinline__ float2 late(int dx, int dy, int dz) const {
+    const float2 *ptr = &rho[idx(dx, dy, dz)];
+    float2 v;
+    asm volatile("ld.global.ca.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(ptr));
+    return v;
+  }
+};
+
+template <int PARITY, int ST, bool PC, int CFG>
+__global__ void __launch_bounds__(WaveShape<ST, CFG>::threads, WaveShape<ST, CFG>::minb)
+    k_wave(StepParams p, Workspace w, WaveArgs a) {
+  using C = Codec2<ST>;
+  using T2 = typename C::T2;
+  constexpr int BY = WaveShape<ST, CFG>::c.by, NT = kTile * BY;
+  extern __shared__ __align__(16) unsigned char wave_smem[];
+  T2(*buf)[kQ][NT] = reinterpret_cast<T2(*)[kQ][NT]>(wave_smem);  // [0] collision, [1] density
+  __shared__ unsigned s_ticket[2], s_epoch;
+  const int tid = threadIdx.y * kTile + threadIdx.x;
+  unsigned *ctl = w.wave, *flag = w.wave + kWaveCtlWords;
+  const T2 *f = static_cast<const T2 *>(w.f);
+  const long long pairs = p.ntiles * kTilePairs, nodes = p.ntiles * kTile;
+  const long long nflags = (long long)p.nz * a.tp;
+  const int nty = a.tp / p.ntx;
+  if (tid == 0) {
+    s_epoch = *(volatile unsigned *)&ctl[2] + 1u;
+    s_ticket[0] = atomicAdd(&ctl[0], 1u);
+  }
+  __syncthreads();
+  const unsigned epoch = s_epoch;
+  unsigned k = s_ticket[0];
+  // populations of node (x, y, z) into buffer b (this thread's own slots)
+  auto copy = [&](int x, int y, int z, int b) {
+    const Geo g = make_geo(p, x, y, z);
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) {
+      const int slot = PARITY == 0 ? i : opp(i);
+      const T2 *src = f + (PARITY == 0 ? g.pop_off(0, 0, 0) : g.pop_off(-cx(i), -cy(i), -cz(i)));
+      if (kChecked && !in_bounds(w.fault, (src - f) + slot * kTile, pairs, kFaultPopLoad))
+        src = f - slot * kTile;
+      cp_async(&buf[b][i][tid], src + slot * kTile);
+    }
+  };
+  auto decode = [&](int b, int own, float (&v1)[kQ], float (&v2)[kQ]) {
+    const float2 own_prev =
+        storage_local(ST)
+            ? __ldg(&w.rho_enc[(kChecked && !in_bounds(w.fault, own, nodes, kFaultRhoLoad)) ? 0 : own])
+            : make_float2(0.f, 0.f);
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) {
+      const float2 v = C::dec(buf[b][i][tid], dec_ref<ST>(p, own_prev, i));
+      v1[i] = v.x;
+      v2[i] = v.y;
+    }
+  };
+  int it = 0;
+  while (k < a.items) {
+    it ^= 1;
+    if (tid == 0) s_ticket[it] = atomicAdd(&ctl[0], 1u);  // next item, read at the end
+    const int grp = (int)(k / (unsigned)a.tp), T = (int)(k % (unsigned)a.tp);
+    const int tx = T % p.ntx, ty = T / p.ntx;
+    const int x = tx * kTile + threadIdx.x, y = ty * BY + threadIdx.y;
+    const bool active = x < p.nx && y < p.ny;
+    const int q = grp - a.lag;                   // plane collided, if >= 0
+    const int zd = grp == 0 ? p.nz - 1 : grp - 1;  // plane summed, if grp < nz
+    const bool has_c = q >= 0, has_d = grp < p.nz;
+    const int xlo = tx * kTile, xhi = min(xlo + kTile, p.nx) - 1;
+    const int ylo = ty * BY, yhi = min(ylo + BY, p.ny) - 1;
+    // one commit group per plane: the collision's first
+    if (has_c && active) copy(x, y, q, 0);
+    cp_async_commit();
+    if (has_d && active) copy(x, y, zd, 1);
+    cp_async_commit();
+    if (has_c && tid < 27) {
+      const int dx = tid % 3 - 1, dy = (tid / 3) % 3 - 1, dz = tid / 9 - 1;
+      const int zz = (q + dz + p.nz) % p.nz, yy = (ty + dy + nty) % nty,
+                xx = (tx + dx + p.ntx) % p.ntx;
+      long long fi = (long long)zz * a.tp + (long long)yy * p.ntx + xx;
+      if (kChecked && !in_bounds(w.fault, fi, nflags, kFaultFlag)) fi = 0;
+      // after one wait has run out the others give up at once
+      unsigned n = 0;
+      while (ld_relaxed(&flag[fi]) != epoch) {
+        if (++n == kWaveSpinLimit) {
+          atomicOr(w.fault, kFaultWait);
+          break;
+        }
+        if ((n & 255u) == 0 && (*(volatile unsigned *)w.fault & kFaultWait)) break;
+        __nanosleep(64);
+      }
+    }
+    __syncthreads();  // the densities the collision reads are published
+    if (has_c && active) {
+      cp_async_wait<1>();
+      const Geo g = make_geo(p, x, y, q);
+      float f1[kQ], f2[kQ];
+      decode(0, g.node(0, 0, 0), f1, f2);
+      reservoir_state(p, box_in_reservoir(p, xlo, xhi, ylo, yhi, q, q), x, y, q, f1, f2);
+      collide_loaded<PARITY, ST, PC, WaveRho>(p, w, g, WaveRho{global_rho(p, w, g)}, f1, f2);
+    }
+    cp_async_wait<0>();
+    if (has_d && active) {
+      const long long own = ((long long)(zd * p.ny + y) * p.ntx + tx) * kTile + threadIdx.x;
+      float v1[kQ], v2[kQ];
+      decode(1, (int)own, v1, v2);
+      reservoir_state(p, box_in_reservoir(p, xlo, xhi, ylo, yhi, zd, zd), x, y, zd, v1, v2);
+      if (in_bounds(w.fault, own, nodes, kFaultRhoStore))
+        w.rho[own] = make_float2(sum19(v1), sum19(v2));
+    }
+    __syncthreads();  // the tile's densities are stored, the buffers free
+    if (has_d && tid == 0) {
+      long long fi = (long long)zd * a.tp + T;
+      if (!kChecked || in_bounds(w.fault, fi, nflags, kFaultFlag)) st_release(&flag[fi], epoch);
+    }
+    k = s_ticket[it];
+  }
+  // The last block out resets the ticket and advances the epoch for the
+  // next launch.
+  if (tid == 0) {
+    __threadfence();
+    if (atomicAdd(&ctl[1], 1u) == gridDim.x - 1) {
+      volatile unsigned *vc = ctl;
+      vc[0] = 0u;
+      vc[1] = 0u;
+      vc[2] = epoch;
+      __threadfence();
+    }
+  }
+}
+
 // ---- single-pass step: density and fused pass in one sweep ----
 //
 // The two-pass step reads every population twice (160 B/node for the

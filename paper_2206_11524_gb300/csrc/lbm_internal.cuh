@@ -196,8 +196,11 @@ struct Workspace {
   float *ads2;       // [ntiles * 32] G_ads,2 * n_s,2, or nullptr
   float *stage;      // [6][nlin] linear (x fastest) staging for host transfers
   double *red;       // [kRedBlocks][kRedK] partial sums + [kRedK] result
-  unsigned *fault;   // bounds-checked builds: bits of the accesses that
-                     // were out of range (FaultBits); unused otherwise
+  unsigned *fault;   // bits of the accesses that were out of range in
+                     // bounds-checked builds, and of wavefront waits that
+                     // ran out in any build (FaultBits)
+  unsigned *wave;    // wavefront step: kWaveCtlWords control words (ticket,
+                     // blocks done, epoch), then the tiles' flags
 };
 
 // Bounds-checked builds (compiled with -DHMCSC_CHECKED) test the index of
@@ -208,7 +211,7 @@ struct Workspace {
 enum FaultBits : unsigned {
   kFaultPopLoad = 1u, kFaultPopStore = 2u, kFaultRhoLoad = 4u,
   kFaultRhoStore = 8u, kFaultGeometry = 16u, kFaultShared = 32u,
-  kFaultStage = 64u
+  kFaultStage = 64u, kFaultWait = 128u, kFaultFlag = 256u
 };
 #ifdef HMCSC_CHECKED
 constexpr bool kChecked = true;
@@ -224,6 +227,16 @@ __device__ __forceinline__ bool in_bounds(unsigned *, long long, long long, unsi
   return true;
 }
 #endif
+
+// Wavefront step: control words ahead of the flags (one per tile of 32 x by
+// nodes of a plane; room for one per x-tile), and the default and smallest
+// lag (planes the densities run ahead of the collisions).
+constexpr int kWaveCtlWords = 64, kWaveLagDefault = 4, kWaveLagMin = 3;
+constexpr int kWaveConfigs = 4;  // shapes 1 .. kWaveConfigs - 1 (0: two passes)
+__host__ __device__ inline long long wave_flag_words(long long nx, long long ny,
+                                                     long long nz) {
+  return nz * ny * ((nx + 31) / 32);
+}
 
 constexpr int kRedBlocks = 304;  // 2 x 152 SMs
 constexpr int kRedThreads = 256;
@@ -279,6 +292,8 @@ cudaError_t launch_batch_collide(const BatchArgs &a, int storage, cudaStream_t s
                                 const float *, const float *, cudaStream_t);   \
   cudaError_t launch_single_pass_##SUF(const StepParams &, const Workspace &,  \
                                        int, int, cudaStream_t);                \
+  cudaError_t launch_wave_##SUF(const StepParams &, const Workspace &, int,     \
+                                int, int, cudaStream_t);                       \
   cudaError_t launch_batch_density_##SUF(const BatchArgs &, cudaStream_t);     \
   cudaError_t launch_batch_collide_##SUF(const BatchArgs &, cudaStream_t);
 HMCSC_DECLARE_STORAGE_LAUNCHERS(f32)
@@ -314,6 +329,12 @@ cudaError_t launch_fields(const StepParams &p, const Workspace &w, int parity,
 constexpr int kSinglePassMaxNx = 256;
 cudaError_t launch_single_pass(const StepParams &p, const Workspace &w, int parity,
                                int nzc, cudaStream_t s);
+// One whole step in one persistent launch (k_wave): densities computed lag
+// planes ahead of the collision, the second read of the populations served
+// by L2.  cfg in 1 .. kWaveConfigs - 1 (wave_cfg), lag >= kWaveLagMin.
+// Leaves the step's densities in w.rho like launch_density.
+cudaError_t launch_wave(const StepParams &p, const Workspace &w, int parity,
+                        int cfg, int lag, cudaStream_t s);
 cudaError_t launch_reduce(const StepParams &p, const Workspace &w,
                           cudaStream_t s);
 

@@ -132,6 +132,7 @@ size_t workspace_bytes(long long nx, long long ny, long long nz, int storage,
   size_t o_ns2 = take(per_component ? sizeof(float) * nt : 0);
   size_t o_ads2 = take(per_component ? sizeof(float) * nt : 0);
   size_t o_fault = take(sizeof(unsigned));
+  size_t o_wave = take(sizeof(unsigned) * (kWaveCtlWords + wave_flag_words(nx, ny, nz)));
   if (out) {
     out->f = (void *)(base + o_f);
     out->rho = (float2 *)(base + o_rho);
@@ -143,6 +144,7 @@ size_t workspace_bytes(long long nx, long long ny, long long nz, int storage,
     out->ns2 = per_component ? (float *)(base + o_ns2) : nullptr;
     out->ads2 = per_component ? (float *)(base + o_ads2) : nullptr;
     out->fault = (unsigned *)(base + o_fault);
+    out->wave = (unsigned *)(base + o_wave);
   }
   return off;
 }
@@ -207,6 +209,17 @@ cudaError_t launch_single_pass(const StepParams &p, const Workspace &w, int pari
     case kF16L: return launch_single_pass_f16l(p, w, parity, nzc, s);
     case kBF16L: return launch_single_pass_bf16l(p, w, parity, nzc, s);
     default: return launch_single_pass_f32(p, w, parity, nzc, s);
+  }
+}
+
+cudaError_t launch_wave(const StepParams &p, const Workspace &w, int parity,
+                        int cfg, int lag, cudaStream_t s) {
+  switch (p.storage) {
+    case kF16: return launch_wave_f16(p, w, parity, cfg, lag, s);
+    case kBF16: return launch_wave_bf16(p, w, parity, cfg, lag, s);
+    case kF16L: return launch_wave_f16l(p, w, parity, cfg, lag, s);
+    case kBF16L: return launch_wave_bf16l(p, w, parity, cfg, lag, s);
+    default: return launch_wave_f32(p, w, parity, cfg, lag, s);
   }
 }
 

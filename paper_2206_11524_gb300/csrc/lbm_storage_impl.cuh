@@ -139,6 +139,74 @@ cudaError_t HMCSC_NAME(launch_single_pass)(const StepParams &p, const Workspace 
   return parity == 0 ? single_pass<0, false>(p, w, nzc, s) : single_pass<1, false>(p, w, nzc, s);
 }
 
+namespace {
+// Resident blocks per SM and SM count of the current device for one k_wave
+// instance (the grid is one wave of persistent blocks).
+struct WaveOccupancy {
+  int dev = -1, per_sm = 0, sms = 0;
+};
+template <int PARITY, bool PC, int CFG>
+cudaError_t wave_launch(const StepParams &p, const Workspace &w, int lag, cudaStream_t s) {
+  using T2 = typename Codec2<kST>::T2;
+  constexpr int BY = wave_cfg(CFG).by, NT = kTile * BY;
+  constexpr int smem = 2 * kQ * NT * (int)sizeof(T2);
+  auto kern = k_wave<PARITY, kST, PC, CFG>;
+  static WaveOccupancy occ[16];
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 16) return cudaErrorInvalidDevice;
+  WaveOccupancy &o = occ[dev];
+  if (o.dev != dev) {
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o.per_sm, kern, NT, smem);
+    if (e == cudaSuccess)
+      e = cudaDeviceGetAttribute(&o.sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    if (o.per_sm < 1) return cudaErrorInvalidConfiguration;
+    o.dev = dev;
+  }
+  WaveArgs a;
+  a.tp = p.ntx * ((p.ny + BY - 1) / BY);
+  a.lag = lag;
+  a.items = (unsigned)((long long)(p.nz + lag) * a.tp);
+  const long long want = (long long)o.per_sm * o.sms;
+  const unsigned grid = (unsigned)(want < (long long)a.items ? want : (long long)a.items);
+  // A cooperative launch: every block is resident while the others run.
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(kTile, BY, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, p, w, a);
+}
+template <int PARITY, int CFG>
+cudaError_t wave_pc(const StepParams &p, const Workspace &w, int lag, cudaStream_t s) {
+  return w.ns2 ? wave_launch<PARITY, true, CFG>(p, w, lag, s)
+               : wave_launch<PARITY, false, CFG>(p, w, lag, s);
+}
+template <int PARITY>
+cudaError_t wave_any(const StepParams &p, const Workspace &w, int cfg, int lag, cudaStream_t s) {
+  switch (cfg) {
+    case 2: return wave_pc<PARITY, 2>(p, w, lag, s);
+    case 3: return wave_pc<PARITY, 3>(p, w, lag, s);
+    default: return wave_pc<PARITY, 1>(p, w, lag, s);
+  }
+}
+}  // namespace
+
+cudaError_t HMCSC_NAME(launch_wave)(const StepParams &p, const Workspace &w, int parity,
+                                    int cfg, int lag, cudaStream_t s) {
+  if (lag < kWaveLagMin) return cudaErrorInvalidValue;
+  return parity == 0 ? wave_any<0>(p, w, cfg, lag, s) : wave_any<1>(p, w, cfg, lag, s);
+}
+
 cudaError_t HMCSC_NAME(launch_batch_density)(const BatchArgs &a, cudaStream_t s) {
   k_batch_density<kST><<<(unsigned)a.prefix[a.n], dim3(kTile, kBatchBY, 1), 0, s>>>(a);
   return cudaGetLastError();

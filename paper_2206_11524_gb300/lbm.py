@@ -39,9 +39,12 @@ ABI_SYMBOLS = (
     "lbm_batch_graph_destroy", "lbm_set_launch_config",
     "lbm_set_geometry_per_component", "lbm_set_bc_velocity", "lbm_set_single_pass",
     "lbm_build_checked", "lbm_fault_word", "lbm_get_launch_config",
+    "lbm_set_wavefront",
 )
 LBM_DENSITY_CONFIGS, LBM_COLLIDE_CONFIGS = 3, 10
 SINGLE_PASS_MAX_NX = 256
+LBM_WAVE_SHAPES = 4
+LBM_FAULT_WAIT = 128
 LBM_BATCH_MAX = 64
 
 
@@ -98,6 +101,7 @@ def load(path: str | None = None):
         "lbm_set_bc_velocity": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int] + [ctypes.c_double] * 5),
         "lbm_step": (ctypes.c_int, [vp, ctypes.c_int]),
         "lbm_set_single_pass": (ctypes.c_int, [vp, ctypes.c_int]),
+        "lbm_set_wavefront": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int]),
         "lbm_build_checked": (ctypes.c_int, []),
         "lbm_get_launch_config": (ctypes.c_int, [vp] + [ctypes.POINTER(ctypes.c_int)] * 3),
         "lbm_fault_word": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_uint32), ctypes.c_int]),
@@ -230,6 +234,10 @@ def lbm_fault_word(ctx, clear=True):
 
 def lbm_set_single_pass(ctx, planes):
     return _check(ctx, load().lbm_set_single_pass(ctx, int(planes)))
+
+
+def lbm_set_wavefront(ctx, shape, lag=0):
+    return _check(ctx, load().lbm_set_wavefront(ctx, int(shape), int(lag)))
 
 
 def lbm_density(ctx):
@@ -425,6 +433,12 @@ class Lattice:
     def set_single_pass(self, planes):
         """Single-pass lbm_step with boxes of `planes` planes (0: two passes)."""
         lbm_set_single_pass(self.ctx, planes)
+
+    def set_wavefront(self, shape, lag=0):
+        """Wavefront lbm_step of tile shape `shape` (1: 32 x 4, 2: 32 x 2,
+        3: 32 x 8 nodes; 0: off) with densities `lag` planes ahead (0:
+        default)."""
+        lbm_set_wavefront(self.ctx, shape, lag)
 
     def set_launch_config(self, density_cfg=0, even_cfg=0, odd_cfg=0):
         lbm_set_launch_config(self.ctx, density_cfg, even_cfg, odd_cfg)

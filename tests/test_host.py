@@ -31,8 +31,9 @@ def test_header_declares_the_binding_symbols():
 
 def test_header_constants_match_the_binding():
     src = open(os.path.join(ROOT, "include", "lbm.h")).read()
-    defs = dict(re.findall(r"^#define\s+(LBM_\w+)\s+(\d+)", src, re.M))
-    for name in ("LBM_DENSITY_CONFIGS", "LBM_COLLIDE_CONFIGS", "LBM_BATCH_MAX"):
+    defs = dict(re.findall(r"^#define\s+(LBM_\w+)\s+(\d+)u?\b", src, re.M))
+    for name in ("LBM_DENSITY_CONFIGS", "LBM_COLLIDE_CONFIGS", "LBM_BATCH_MAX",
+                 "LBM_WAVE_SHAPES", "LBM_FAULT_WAIT"):
         assert int(defs[name]) == getattr(lbm, name), name
 
 
