@@ -320,11 +320,13 @@ def run_gpu(args, world, rank, local):
     single = args.single_pass > 0
     if single:
         lat.set_single_pass(args.single_pass)
-    wave = None
     if args.wavefront:
-        wave = [int(v) for v in args.wavefront.split(",")] + [0]
-        wave = wave[:2]
-        lat.set_wavefront(*wave)
+        lat.set_wavefront(*([int(v) for v in args.wavefront.split(",")] + [0])[:2])
+    elif args.no_wavefront:
+        lat.set_wavefront(0)
+    wave = list(lat.wavefront())          # the step in use (tuned or asked for)
+    if wave[0] == 0 or single:
+        wave = None
     one_launch = single or wave is not None
     for _ in range(args.warmup):
         if one_launch:
@@ -447,7 +449,7 @@ def run_gpu(args, world, rank, local):
                          f"{lat.workspace.numel() / 1e9:.2f} GB)",
                    "parallelism": f"replicas x{world}",
                    "launch_config": launch,
-                   "wavefront": ({"shape": wave[0], "lag": wave[1] or 4}
+                   "wavefront": ({"shape": wave[0], "lag": wave[1]}
                                  if wave is not None else None)},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak,
@@ -493,6 +495,8 @@ def main(argv=None):
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--wavefront", default="",
                     help="time the wavefront step: SHAPE[,LAG] (see lbm_set_wavefront)")
+    ap.add_argument("--no-wavefront", action="store_true",
+                    help="time the two-pass step even where the tuner picks the wavefront")
     ap.add_argument("--single-pass", type=int, default=0,
                     help="time the single-pass step with boxes of about this many planes")
     ap.add_argument("--launch-config", default="",

@@ -202,6 +202,9 @@ LBM_API lbm_status lbm_set_single_pass(lbm_ctx *ctx, int planes);
 #define LBM_WAVE_SHAPES 4
 #define LBM_FAULT_WAIT 128u
 LBM_API lbm_status lbm_set_wavefront(lbm_ctx *ctx, int shape, int lag);
+/* The wavefront shape (0: off) and lag in use, to *shape and *lag (either
+ * may be NULL).  Errors: EINVAL (NULL ctx). */
+LBM_API lbm_status lbm_get_wavefront(const lbm_ctx *ctx, int *shape, int *lag);
 
 /* The two halves of one step, for callers that time or interleave them:
  * lbm_density (rho_sigma of Eq. A.4 at every node) followed by

@@ -1,6 +1,7 @@
 """Autotuner of the launch shapes (thread-block shape and register budget) of
-the density pass and of the fused pass on even and odd steps, and
-optionally of the choice between the two-pass and the single-pass step.
+the density pass and of the fused pass on even and odd steps, of the choice
+between the two-pass step and the wavefront step (one persistent launch),
+and optionally of the single-pass step.
 
 `tune(nx, ny, nz, storage)` times every shape on a scratch lattice of that
 size and storage (a synthetic gray medium with two-phase densities; the
@@ -113,12 +114,19 @@ def _single_pass_candidates(ny, nz, sms):
     return out
 
 
-def tune(nx, ny, nz, storage="f32", reps=10, single_pass=False, margin=0.03):
-    """Fastest (density, even, odd) launch shapes and all timings (ms).  With
-    single_pass, whole steps of the best two-pass shapes are timed against
-    the single-pass step at box depths that fit the SM count; a single-pass
-    depth is kept (fourth entry, 0 = two passes) only if it is faster by
-    more than `margin`."""
+# Wavefront (shape, lag) pairs the tuner weighs against the two-pass step.
+WAVE_CANDIDATES = ((2, 4), (1, 4), (2, 5), (3, 4))
+
+
+def tune(nx, ny, nz, storage="f32", reps=10, single_pass=False, margin=0.03,
+         wavefront=True):
+    """Fastest (density, even, odd) launch shapes and all timings (ms),
+    extended to (density, even, odd, single-pass depth, wavefront shape,
+    wavefront lag).  Whole steps of the best two-pass shapes are timed
+    against the wavefront step at WAVE_CANDIDATES (with `wavefront`) and, with
+    single_pass, against the single-pass step at box depths that fit the SM
+    count; another step than the two-pass one is kept only if it is faster by
+    more than `margin` (single-pass depth 0 and wavefront shape 0 otherwise)."""
     lat = _scratch(nx, ny, nz, storage)
     ctx = lat.ctx
     timings = {"density": [], "even": [], "odd": []}
@@ -154,38 +162,51 @@ def tune(nx, ny, nz, storage="f32", reps=10, single_pass=False, margin=0.03):
         timings["odd"].append(fused_only(1))
     best_o = int(np.argmin(timings["odd"]))
     cfg = (best_d, best_e, best_o)
-    if single_pass and nx <= lbm.SINGLE_PASS_MAX_NX:
-        import torch
+    best_sp, best_wave = 0, (0, 0)
+    if single_pass or wavefront:
         lbm.lbm_set_launch_config(ctx, *cfg)
         two = _step_ms(lat)
         timings["two_pass_step"] = two
-        best_sp, best_ms = 0, two * (1.0 - margin)
-        sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
-        for planes in _single_pass_candidates(ny, nz, sms):
-            lat.set_single_pass(planes)
-            ms = _step_ms(lat)
-            timings[f"single_pass_{planes}"] = ms
-            if ms < best_ms:
-                best_sp, best_ms = planes, ms
-        lat.set_single_pass(0)
-        cfg = cfg + (best_sp,)
+        best_ms = two * (1.0 - margin)
+        if wavefront:
+            for shape, lag in WAVE_CANDIDATES:
+                lat.set_wavefront(shape, lag)
+                ms = _step_ms(lat)
+                timings[f"wavefront_{shape}_{lag}"] = ms
+                if ms < best_ms:
+                    best_wave, best_ms = (shape, lag), ms
+            lat.set_wavefront(0)
+        if single_pass and nx <= lbm.SINGLE_PASS_MAX_NX:
+            import torch
+            sms = torch.cuda.get_device_properties(
+                torch.cuda.current_device()).multi_processor_count
+            for planes in _single_pass_candidates(ny, nz, sms):
+                lat.set_single_pass(planes)
+                ms = _step_ms(lat)
+                timings[f"single_pass_{planes}"] = ms
+                if ms < best_ms:
+                    best_sp, best_wave, best_ms = planes, (0, 0), ms
+            lat.set_single_pass(0)
     lat.close()
-    return cfg, timings
+    return cfg + (best_sp,) + best_wave, timings
 
 
 def apply(lattice, table: TuneTable | None = None, tune_if_missing=True,
-          single_pass=False):
+          single_pass=False, wavefront=True):
     """Configure `lattice` from the table, tuning (and recording) its size
     and storage first when the table has no entry.  An entry's optional
-    fourth value is the single-pass box depth (0: two passes)."""
+    fourth value is the single-pass box depth (0: two passes), its optional
+    fifth and sixth the wavefront shape (0: off) and lag."""
     table = table or TuneTable()
     nz, ny, nx = lattice.shape
     storage = lattice.storage_name
     cfg = table.get(nx, ny, nz, storage)
     if cfg is None and tune_if_missing:
-        cfg, timings = tune(nx, ny, nz, storage, single_pass=single_pass)
+        cfg, timings = tune(nx, ny, nz, storage, single_pass=single_pass,
+                            wavefront=wavefront)
         table.put(nx, ny, nz, storage, cfg, timings)
     if cfg is not None:
         lbm.lbm_set_launch_config(lattice.ctx, *cfg[:3])
         lattice.set_single_pass(cfg[3] if len(cfg) > 3 else 0)
+        lattice.set_wavefront(*(cfg[4:6] if len(cfg) > 5 else (0, 0)))
     return cfg

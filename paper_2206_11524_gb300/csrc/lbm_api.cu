@@ -589,6 +589,13 @@ lbm_status lbm_set_wavefront(lbm_ctx *c, int shape, int lag) {
   return LBM_OK;
 }
 
+lbm_status lbm_get_wavefront(const lbm_ctx *c, int *shape, int *lag) {
+  if (!c) return LBM_EINVAL;
+  if (shape) *shape = c->wave_cfg;
+  if (lag) *lag = c->wave_lag;
+  return LBM_OK;
+}
+
 int64_t lbm_time(const lbm_ctx *c) { return c ? c->t : -1; }
 
 lbm_status lbm_read_fields(lbm_ctx *c, float *rho_a, float *rho_b, float *u,

@@ -822,18 +822,20 @@ __global__ void k_init_equilibrium(StepParams p, Workspace w,
 //     eight in-plane neighbour tiles are published, then collides and
 //     streams plane q of T exactly as k_collide_stream does,
 //   - sums the populations of plane d(g) into the density array and
-//     publishes them: the flag of (d(g), T) is set to the launch's epoch.
+//     publishes them: after a block barrier one thread sets the flag of
+//     (d(g), T) to the launch's epoch with a release store.
 // The densities a collision of plane q needs come from groups q .. q + 2,
 // all before g when lag >= 3, so an item waits only on items with smaller
 // tickets; those are held by blocks that are already running, so the launch
 // cannot deadlock for any number of resident blocks (every wait is bounded
-// all the same).  The populations of plane q were read from DRAM by the
-// density part lag - 1 groups earlier (a group is one plane of the lattice,
-// 10 MB at 256^2 in float32) and the collision finds them in L2: one step
-// moves its populations through DRAM once instead of twice.  In-place AA
-// streaming stays race-free: the collision of node n touches only the slots
-// holding n's own populations, whose density part has finished reading
-// them before n's flag is set.
+// all the same, and the launch is cooperative, so every block is resident
+// anyway).  The populations of plane q were read from DRAM by the density
+// part lag - 1 groups earlier (a group is one plane of the lattice, 10 MB at
+// 256^2 in float32) and the collision finds them in L2: one step moves its
+// populations through DRAM once instead of twice.  In-place AA streaming
+// stays race-free: the collision of node n touches only the slots holding
+// n's own populations, whose density part has finished reading them before
+// n's flag is set.
 struct WaveCfg {
   int by, minb, minb_local;
 };
@@ -851,10 +853,19 @@ struct WaveArgs {
   int tp;          // tiles per plane: ntx * ceil(ny / by)
   int lag;
 };
-// Polls of one flag before a wait gives up (about a second with the
+// Polls of one flag before a wait gives up (a few seconds at most with the
 // back-off); the item then goes on and the fault word records kFaultWait.
 constexpr unsigned kWaveSpinLimit = 1u << 22;
 
+// Flags are polled with relaxed loads, served by L2, so polling leaves the
+// SM's L1 alone (an acquire would drop it, and with it the stencil's cached
+// densities and geometry, once per poll).  A flag is set by a release store
+// after the tile's density stores, so once a poll sees the epoch those
+// densities are in L2; the loads that read them are issued after the poll
+// returned, and no SM caches a line of a tile's densities in L1 before that
+// tile's flag is set in this launch (each 128-byte line belongs to one
+// tile, and L1 is invalidated between launches), so they miss L1 the first
+// time and read L2.
 __device__ __forceinline__ unsigned ld_relaxed(const unsigned *ptr) {
   unsigned v;
   asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(ptr) : "memory");
@@ -864,8 +875,8 @@ __device__ __forceinline__ void st_release(unsigned *ptr, unsigned v) {
   asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(ptr), "r"(v) : "memory");
 }
 
-// Densities written earlier in the same launch by other blocks: coherent
-// loads (the flag's acquire orders them), cached in L1 for the stencil.
+// Densities written earlier in the same launch by other blocks, read after
+// their flags (see above), cached in L1 for the stencil.
 struct WaveRho : GlobalRho {
   __device__ __forceinline__ float2 at(int dx, int dy, int dz) const {
     return __ldca(&rho[idx(dx, dy, dz)]);

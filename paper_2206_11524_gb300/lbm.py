@@ -39,7 +39,7 @@ ABI_SYMBOLS = (
     "lbm_batch_graph_destroy", "lbm_set_launch_config",
     "lbm_set_geometry_per_component", "lbm_set_bc_velocity", "lbm_set_single_pass",
     "lbm_build_checked", "lbm_fault_word", "lbm_get_launch_config",
-    "lbm_set_wavefront",
+    "lbm_set_wavefront", "lbm_get_wavefront",
 )
 LBM_DENSITY_CONFIGS, LBM_COLLIDE_CONFIGS = 3, 10
 SINGLE_PASS_MAX_NX = 256
@@ -102,6 +102,7 @@ def load(path: str | None = None):
         "lbm_step": (ctypes.c_int, [vp, ctypes.c_int]),
         "lbm_set_single_pass": (ctypes.c_int, [vp, ctypes.c_int]),
         "lbm_set_wavefront": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int]),
+        "lbm_get_wavefront": (ctypes.c_int, [vp] + [ctypes.POINTER(ctypes.c_int)] * 2),
         "lbm_build_checked": (ctypes.c_int, []),
         "lbm_get_launch_config": (ctypes.c_int, [vp] + [ctypes.POINTER(ctypes.c_int)] * 3),
         "lbm_fault_word": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_uint32), ctypes.c_int]),
@@ -238,6 +239,12 @@ def lbm_set_single_pass(ctx, planes):
 
 def lbm_set_wavefront(ctx, shape, lag=0):
     return _check(ctx, load().lbm_set_wavefront(ctx, int(shape), int(lag)))
+
+
+def lbm_get_wavefront(ctx):
+    shape, lag = ctypes.c_int(0), ctypes.c_int(0)
+    _check(ctx, load().lbm_get_wavefront(ctx, ctypes.byref(shape), ctypes.byref(lag)))
+    return shape.value, lag.value
 
 
 def lbm_density(ctx):
@@ -439,6 +446,10 @@ class Lattice:
         3: 32 x 8 nodes; 0: off) with densities `lag` planes ahead (0:
         default)."""
         lbm_set_wavefront(self.ctx, shape, lag)
+
+    def wavefront(self):
+        """(shape, lag) of the wavefront step in use (shape 0: off)."""
+        return lbm_get_wavefront(self.ctx)
 
     def set_launch_config(self, density_cfg=0, even_cfg=0, odd_cfg=0):
         lbm_set_launch_config(self.ctx, density_cfg, even_cfg, odd_cfg)

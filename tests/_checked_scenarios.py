@@ -57,6 +57,13 @@ def run():
     g.set_single_pass(3)
     g.step(4)
     keep("single", g)
+    for k, (shape, st, wave) in enumerate([((6, 17, 100), "f32", (2, 0)),
+                                           ((5, 9, 37), "f16l", (1, 3)),
+                                           ((3, 4, 7), "bf16", (3, 6))]):
+        g = _lattice(shape, st, seed=30 + k)
+        g.set_wavefront(*wave)
+        g.step(3)
+        keep(f"wave{k}", g)
     for cfg in ((2, 3, 3), (1, 1, 1), (0, 2, 2), (0, 6, 7), (0, 8, 9), (0, 5, 5), (0, 4, 4)):
         g = _lattice((5, 9, 40), "f16l", seed=13)
         g.set_launch_config(*cfg)

@@ -51,7 +51,9 @@ def test_autotune_records_and_applies(tmp_path):
     g.set_geometry(np.zeros((40, 48, 64)))
     g.init_equilibrium(np.ones((40, 48, 64)), np.ones((40, 48, 64)))
     cfg = g.autotune(table)
-    assert len(cfg) == 3
+    assert len(cfg) == 6 and cfg[3] == 0          # no single-pass unless asked
+    assert g.wavefront()[0] == cfg[4]
+    assert cfg[4] == 0 or (cfg[4], cfg[5]) in autotune.WAVE_CANDIDATES
     again = autotune.TuneTable(str(tmp_path / "t.json"))
     assert again.get(64, 48, 40, "f32") == tuple(cfg)
     with pytest.raises(lbm.LbmError):
@@ -61,8 +63,9 @@ def test_autotune_records_and_applies(tmp_path):
 
 
 def test_autotune_weighs_the_single_pass(tmp_path):
-    """With single_pass the table entry gets a fourth value (box depth or 0)
-    and applying it gives the same populations as the defaults."""
+    """With single_pass the table entry's fourth value is a box depth or 0
+    (the fifth and sixth the wavefront shape and lag), and applying it gives
+    the same populations as the defaults."""
     table = autotune.TuneTable(str(tmp_path / "t.json"))
     shape = (40, 48, 64)
     ns, gads = synth.random_geometry(shape, 3)
@@ -74,7 +77,8 @@ def test_autotune_weighs_the_single_pass(tmp_path):
         g.set_populations(f0)
         if tuned:
             cfg = g.autotune(table, single_pass=True)
-            assert len(cfg) == 4 and cfg[3] >= 0
+            assert len(cfg) == 6 and cfg[3] >= 0
+            assert not (cfg[3] > 0 and cfg[4] > 0)   # one step kind at most
         g.step(3)
         out.append(g.populations())
         g.close()
