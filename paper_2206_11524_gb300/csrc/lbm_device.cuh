@@ -953,8 +953,10 @@ __global__ void __launch_bounds__(WaveShape<ST, CFG>::threads, WaveShape<ST, CFG
     cp_async_commit();
     if (has_d && active) copy(x, y, zd, 1);
     cp_async_commit();
-    if (has_c && tid < 27) {
-      const int dx = tid % 3 - 1, dy = (tid / 3) % 3 - 1, dz = tid / 9 - 1;
+    // every warp waits for the 27 tiles' densities itself
+    if (has_c && threadIdx.x < 27) {
+      const int l = threadIdx.x;
+      const int dx = l % 3 - 1, dy = (l / 3) % 3 - 1, dz = l / 9 - 1;
       const int zz = (q + dz + p.nz) % p.nz, yy = (ty + dy + nty) % nty,
                 xx = (tx + dx + p.ntx) % p.ntx;
       long long fi = (long long)zz * a.tp + (long long)yy * p.ntx + xx;
@@ -970,7 +972,7 @@ __global__ void __launch_bounds__(WaveShape<ST, CFG>::threads, WaveShape<ST, CFG
         __nanosleep(64);
       }
     }
-    __syncthreads();  // the densities the collision reads are published
+    __syncwarp();  // the densities this warp's collisions read are published
     if (has_c && active) {
       cp_async_wait<1>();
       const Geo g = make_geo(p, x, y, q);
