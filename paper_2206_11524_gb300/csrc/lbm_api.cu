@@ -582,7 +582,7 @@ lbm_status lbm_set_wavefront(lbm_ctx *c, int shape, int lag) {
   if (lag == 0) lag = hmcsc::kWaveLagDefault;
   if (lag < hmcsc::kWaveLagMin)
     return fail(c, LBM_EINVAL, "wavefront lag must be >= %d", hmcsc::kWaveLagMin);
-  if ((long long)(c->params.nz + lag) * c->sp.ntx * c->params.ny > 4294967295LL)
+  if (((long long)c->params.nz + lag) * c->sp.ntx * c->params.ny > 4294967295LL)
     return fail(c, LBM_EINVAL, "wavefront lag too large for this lattice");
   c->wave_cfg = shape;
   c->wave_lag = lag;

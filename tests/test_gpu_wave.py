@@ -136,7 +136,7 @@ def test_wave_graph_replay():
 
 def test_wave_rejects_bad_arguments():
     g = lbm.Lattice(8, 4, 4)
-    for shape, lag in ((4, 0), (-1, 0), (1, 2), (1, -3)):
+    for shape, lag in ((4, 0), (-1, 0), (1, 2), (1, -3), (1, 2**31 - 1)):
         with pytest.raises(lbm.LbmError):
             g.set_wavefront(shape, lag)
     g.set_wavefront(0)
