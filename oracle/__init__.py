@@ -3,7 +3,7 @@
 TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
 CPU-baseline / reference legs of ``bench.py`` may import this package.  It is
 the plain, slow statement of the method (``hmcsc_oracle.c``, compiled with gcc
-``-O2 -ffp-contract=off``) against which the CUDA library is judged; it shares
+``-O2 -ffp-contract=off``) against which the CUDA library is checked; it shares
 no code with that library and the library never falls back to it.
 
 Every array here is float64 numpy in the layout of the paper's lattice:

@@ -4,7 +4,7 @@
  *
  * TEST INFRASTRUCTURE ONLY.  This file is the slow, obviously correct
  * statement of what the method computes; the test suite, the smoke check and
- * the CPU-baseline leg of the benchmark use it to judge the CUDA path.  The
+ * the CPU-baseline leg of the benchmark use it to check the CUDA path.  The
  * product path never links, loads or calls it, and it shares no code, header,
  * table or helper with the CUDA library.
  *
