@@ -3,8 +3,10 @@
 Workload: the synthetic 256^3 electrode-imbibition problem (Boolean model of
 solid spheres, gray binder blobs with per-blob n_s, reservoirs at x = 0 and
 x = 255, Table 1 parameters), float32 populations.  A benchmark step is one
-lattice time step over the whole domain: the density pass and the fused
-force/collide/bounce-back/stream pass.
+lattice time step over the whole domain in the form the autotuner picks:
+the wavefront launch (density sums and the fused force/collide/bounce-back/
+stream work in one persistent launch) or the density pass followed by the
+fused pass (``--no-wavefront`` keeps the two passes).
 
 Prints one JSON line:
   value    aggregate MLUPS (lattice node updates per second / 1e6, both
@@ -12,8 +14,9 @@ Prints one JSON line:
   e2e      the same metric through the C ABI with host buffers: geometry and
            density upload, the steps, and the field read-back inside the
            timed region;
-  roofline the fused pass's algorithmic bytes per launch over its average
-           launch duration, against the measured HBM copy bandwidth;
+  roofline the dominant launch's algorithmic bytes over its average
+           duration (the wavefront launch, or the fused pass of the two-pass
+           step), against the measured HBM copy bandwidth;
   cpu_baseline  the FP64 oracle on the host cores on a bounded sample.
 
 ``--impl reference`` times the FP64 CPU oracle instead (rank 0 only).
@@ -43,6 +46,8 @@ UNIT = "MLUPS"
 #   density pass: read 2 x 19 x 4, write 2 x 4              = 160
 #   fused pass:   read 2 x 19 x 4 + rho 8 + n_s 4 + a 4,
 #                 write 2 x 19 x 4                          = 320
+#   wavefront launch (whole step): read 2 x 19 x 4 + n_s 4 + a 4,
+#                 write 2 x 19 x 4 + rho 8                  = 320
 BYTES_DENSITY = 160
 BYTES_COLLIDE = 320
 # 16-bit storages (2 B per population): offset kinds 84 / 168; local kinds
