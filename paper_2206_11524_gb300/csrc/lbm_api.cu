@@ -14,6 +14,7 @@
 
 #include "lbm.h"
 #include "lbm_internal.cuh"
+#include "lbm_validate.h"
 
 using hmcsc::kFaces;
 using hmcsc::kQ;
@@ -302,15 +303,16 @@ lbm_status lbm_set_geometry_per_component(lbm_ctx *c, const float *ns1,
                 "per-component n_s needs a context created with ns_per_component = 1");
   const float *fields[2] = {ns1, ns2};
   for (int k = 0; k < 2; ++k)
-    if (fields[k])
-      for (long long n = 0; n < c->N; ++n)
-        if (!(fields[k][n] >= 0.0f && fields[k][n] <= 1.0f))
-          return fail(c, LBM_EINVAL, "n_s,%d[%lld] = %g is outside [0, 1]", k + 1, n,
-                      (double)fields[k][n]);
-  if (gads2)
-    for (long long n = 0; n < c->N; ++n)
-      if (!std::isfinite(gads2[n]))
-        return fail(c, LBM_EINVAL, "gads2[%lld] is not finite", n);
+    if (fields[k]) {
+      const long long n = hmcsc::first_bad(fields[k], c->N, hmcsc::BadFraction{});
+      if (n < c->N)
+        return fail(c, LBM_EINVAL, "n_s,%d[%lld] = %g is outside [0, 1]", k + 1, n,
+                    (double)fields[k][n]);
+    }
+  if (gads2) {
+    const long long n = hmcsc::first_bad(gads2, c->N, hmcsc::BadFinite{});
+    if (n < c->N) return fail(c, LBM_EINVAL, "gads2[%lld] is not finite", n);
+  }
   const size_t L = lin_stride(c);
   lbm_status st = upload(c, c->ws.stage, ns1, (size_t)c->N);
   if (st) return st;
@@ -344,10 +346,13 @@ lbm_status lbm_init_equilibrium(lbm_ctx *c, const float *rho_a,
                                 const float *rho_b) {
   if (!c) return LBM_EINVAL;
   if (!rho_a || !rho_b) return fail(c, LBM_EINVAL, "density array is NULL");
-  for (long long n = 0; n < c->N; ++n)
-    if (!(rho_a[n] > 0.0f) || !(rho_b[n] > 0.0f) || !std::isfinite(rho_a[n]) ||
-        !std::isfinite(rho_b[n]))
+  {
+    const long long na = hmcsc::first_bad(rho_a, c->N, hmcsc::BadDensity{});
+    const long long nb = hmcsc::first_bad(rho_b, c->N, hmcsc::BadDensity{});
+    const long long n = na < nb ? na : nb;
+    if (n < c->N)
       return fail(c, LBM_EINVAL, "densities at node %lld must be finite and > 0", n);
+  }
   const size_t L = lin_stride(c);
   lbm_status st = upload(c, c->ws.stage, rho_a, (size_t)c->N);
   if (st) return st;
