@@ -1,6 +1,8 @@
 // lbm_storage_impl.cuh -- launchers of the storage-typed kernels for one
 // storage kind.  Included once per kind by lbm_st_*.cu with HMCSC_ST (a
 // StorageKind) and HMCSC_SUF (the name suffix) defined.
+#include <mutex>
+
 #include "lbm_device.cuh"
 
 #define HMCSC_CAT2(a, b) a##_##b
@@ -152,10 +154,12 @@ cudaError_t wave_launch(const StepParams &p, const Workspace &w, int lag, cudaSt
   constexpr int smem = 2 * kQ * NT * (int)sizeof(T2);
   auto kern = k_wave<PARITY, kST, PC, CFG>;
   static WaveOccupancy occ[16];
+  static std::mutex occ_mu;  // host threads may launch on a device first at once
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= 16) return cudaErrorInvalidDevice;
+  std::unique_lock<std::mutex> lock(occ_mu);
   WaveOccupancy &o = occ[dev];
   if (o.dev != dev) {
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -167,11 +171,13 @@ cudaError_t wave_launch(const StepParams &p, const Workspace &w, int lag, cudaSt
     if (o.per_sm < 1) return cudaErrorInvalidConfiguration;
     o.dev = dev;
   }
+  const int per_sm = o.per_sm, sms = o.sms;
+  lock.unlock();
   WaveArgs a;
   a.tp = p.ntx * ((p.ny + BY - 1) / BY);
   a.lag = lag;
   a.items = (unsigned)((long long)(p.nz + lag) * a.tp);
-  const long long want = (long long)o.per_sm * o.sms;
+  const long long want = (long long)per_sm * sms;
   const unsigned grid = (unsigned)(want < (long long)a.items ? want : (long long)a.items);
   // A cooperative launch: every block is resident while the others run.
   cudaLaunchAttribute attr[1];
