@@ -170,7 +170,10 @@ LBM_API lbm_status lbm_set_bc_velocity(lbm_ctx *ctx, int face, int layers,
  * the context's stream.  Each step launches the density pass and the fused
  * force/collide/bounce-back/stream pass, or the single-pass sweep when
  * lbm_set_single_pass enabled it, or the wavefront launch when
- * lbm_set_wavefront enabled it.  n_steps = 0 is a no-op. */
+ * lbm_set_wavefront enabled it.  n_steps = 0 is a no-op.  EINTERNAL (and
+ * nothing enqueued) when a device fault was reported for the current state:
+ * by a synchronising call (below), or by a wavefront launch that already
+ * ran, through a host-mapped word the kernel sets (no stream wait). */
 LBM_API lbm_status lbm_step(lbm_ctx *ctx, int n_steps);
 
 /* Single-pass stepping for lbm_step (planes > 0; 0 = two passes, the
@@ -194,14 +197,27 @@ LBM_API lbm_status lbm_set_single_pass(lbm_ctx *ctx, int planes);
  * workspace), so the second read of each plane's populations comes from L2
  * instead of DRAM.  lag = 0 takes the default (4); other values must be
  * >= 3 (EINVAL otherwise); shapes outside 0..3 are EINVAL.  Results are
- * bit-identical to the two-pass step.  Every wait in the launch is bounded:
- * a wait that runs out (which a correct launch never does) leaves that
- * step's result undefined and sets bit 128 (LBM_FAULT_WAIT) of the word
- * lbm_fault_word reads, in every build.  lbm_density / lbm_collide_stream
- * and the batched entry points keep the two passes. */
+ * bit-identical to the two-pass step.  Contexts on the wavefront step also
+ * advance together in one launch per step in lbm_batch_step.  Every wait in
+ * the launch is bounded: a wait that runs out (which a correct launch never
+ * does) leaves that step's result undefined, sets bit 128 (LBM_FAULT_WAIT)
+ * of the word lbm_fault_word reads, in every build, and makes the next
+ * synchronising call and lbm_step return EINTERNAL.  lbm_density /
+ * lbm_collide_stream keep the two passes. */
 #define LBM_WAVE_SHAPES 4
 #define LBM_FAULT_WAIT 128u
 LBM_API lbm_status lbm_set_wavefront(lbm_ctx *ctx, int shape, int lag);
+
+/* For tests of the failure path of the wavefront step: spin_limit = polls
+ * of one flag before a wait gives up (0 = the default, 2^22, seconds of
+ * waiting); withhold_flag = index plane * T + (y / by) * ceil(nx / 32) +
+ * x / 32, T = ceil(ny / by) * ceil(nx / 32), of one tile's density flag that
+ * the launch then never publishes, so the collisions that read those
+ * densities wait until their limit runs out (-1 = none, the default).  In a
+ * batch they apply when this context is the first one.  EINVAL if the index
+ * is outside the flag words. */
+LBM_API lbm_status lbm_set_wavefront_limits(lbm_ctx *ctx, uint32_t spin_limit,
+                                            int64_t withhold_flag);
 /* The wavefront shape (0: off) and lag in use, to *shape and *lag (either
  * may be NULL).  Errors: EINVAL (NULL ctx). */
 LBM_API lbm_status lbm_get_wavefront(const lbm_ctx *ctx, int *shape, int *lag);
@@ -216,6 +232,14 @@ LBM_API lbm_status lbm_collide_stream(lbm_ctx *ctx);
 
 /* Time steps taken since the last init / set_populations / load. */
 LBM_API int64_t lbm_time(const lbm_ctx *ctx);
+
+/* Synchronising calls (lbm_read_fields, lbm_reduce, lbm_sync,
+ * lbm_get_populations, lbm_save) read the fault word once the stream has
+ * drained and return EINTERNAL when a bit is set: LBM_FAULT_WAIT (the state
+ * is undefined) in any build, an out-of-range access in a bounds-checked
+ * build.  Their outputs are filled all the same.  lbm_init_equilibrium,
+ * lbm_set_populations and lbm_load replace the state and clear
+ * LBM_FAULT_WAIT. */
 
 /* Macroscopic fields of the current state, to host arrays (any may be NULL):
  * rho_a[N], rho_b[N] (Eq. A.4); u[3][N] = u_macro of Eq. 7 (x, y, z planes);
@@ -265,13 +289,16 @@ LBM_API lbm_status lbm_get_launch_config(const lbm_ctx *ctx, int *density_cfg,
 
 /* ---- Batched stepping of independent lattices ---------------------------
  * Several contexts (up to LBM_BATCH_MAX, same storage kind, geometry and
- * state set) advance together: each step is one density launch and one
- * fused launch covering every lattice, whatever their sizes and AA
- * parities.  Each lattice computes exactly what lbm_step computes for it
- * alone.  Work goes on `cuda_stream`; the contexts' own streams are not
- * used, so the caller orders the batch after earlier work on them.
- * EINVAL: bad count, NULL or repeated context, mixed storage; ESTATE: a
- * context without geometry or state. */
+ * state set) advance together, whatever their sizes and AA parities: when
+ * every context uses the wavefront step (lbm_set_wavefront), each step is
+ * one persistent wavefront launch over the tiles of all the lattices at
+ * each AA parity present (in the first context's shape and lag); otherwise
+ * one density launch and one fused launch cover every lattice.  Each
+ * lattice computes exactly what lbm_step computes for it alone.  Work goes
+ * on `cuda_stream`; the contexts' own streams are not used, so the caller
+ * orders the batch after earlier work on them.  EINVAL: bad count, NULL or
+ * repeated context, mixed storage; ESTATE: a context without geometry or
+ * state; EINTERNAL: a context whose state a wavefront wait left undefined. */
 #define LBM_BATCH_MAX 64
 LBM_API lbm_status lbm_batch_step(lbm_ctx *const *ctxs, int n, int n_steps,
                                   void *cuda_stream);
@@ -310,18 +337,20 @@ LBM_API lbm_status lbm_fault_word(lbm_ctx *ctx, uint32_t *out, int clear);
  * that cannot call cudaMalloc where they need the observables -- a host
  * framework that only lends out its own fixed buffers, a real-time loop in
  * which an allocation would stall the device, a plugin that never owns a
- * workspace.  It computes what lbm_reduce computes (masses, S_1 of Eq. 19,
- * reservoir mean pressures of Eq. A.6, non-finite count) from density fields
- * the caller already holds on the device, and allocates nothing: its scratch
- * is a fixed array of about 360 KB inside the library's device image, which
- * every GPU that loads the library keeps until the process exits.
+ * workspace.  It computes the same observables as lbm_reduce (the two
+ * masses, the saturation, the reservoir mean pressures, the non-finite
+ * count; see lbm_observables) from density fields the caller already holds
+ * on the device, and allocates nothing: its scratch is a fixed array of
+ * about 360 KB inside the library's device image, which every GPU that loads
+ * the library keeps until the process exits.
  *
  *   d_rho_a, d_rho_b, d_ns  device arrays [N] (float32, x fastest), read only
  *   nx, ny, nz              lattice size, N = nx*ny*nz <= LBM_NOALLOC_MAX_NODES
  *                           (larger lattices return LBM_ETOOLARGE, nothing run)
  *   layers[6]               reservoir layers per face (-x,+x,-y,+y,-z,+z) as
  *                           given to lbm_set_bc; NULL = no reservoirs
- *   G                       G_inter,12 for the pressure of Eq. A.6
+ *   G                       the context's G, for the pressure; rounded to
+ *                           float as a context holds it
  *   cuda_stream             stream to run on (NULL = legacy default stream)
  *   out                     host result; waits for the stream
  *

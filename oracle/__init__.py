@@ -72,8 +72,10 @@ def _load():
         lib.orc_run.argtypes = [pp, dp, dp, dp, dp, dp, dp, ctypes.c_int]
         lib.orc_fields.argtypes = [pp, dp, dp, dp, dp, dp, dp, dp, dp, dp]
         lib.orc_observables.argtypes = [pp, dp, dp, dp, dp]
+        lib.orc_observables_rho.argtypes = [pp, dp, dp, dp]
         for name in ("orc_lattice", "orc_feq", "orc_init_equilibrium",
-                     "orc_step", "orc_run", "orc_fields", "orc_observables"):
+                     "orc_step", "orc_run", "orc_fields", "orc_observables",
+                     "orc_observables_rho"):
             getattr(lib, name).restype = None
         _lib = lib
     return _lib
@@ -84,6 +86,21 @@ def _ptr(a):
         return None
     assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
     return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def observables_of_densities(params: Params, ns, rho_a, rho_b):
+    """The observables of Sec. 4 (masses, S_1 of Eq. 19, reservoir mean
+    pressures of Eq. A.6) of given density fields [nz, ny, nx], with n_s,1 =
+    ns weighting S_1: the second half of Sim.observables, for densities
+    that do not come from an oracle state."""
+    shape = (params.nz, params.ny, params.nx)
+    rho = np.ascontiguousarray(np.stack([np.asarray(rho_a, np.float64).reshape(shape),
+                                         np.asarray(rho_b, np.float64).reshape(shape)]))
+    ns_c = np.ascontiguousarray(np.asarray(ns, np.float64).reshape(shape))
+    out = np.zeros(9)
+    cp = params.c_struct()
+    _load().orc_observables_rho(ctypes.byref(cp), _ptr(ns_c), _ptr(rho), _ptr(out))
+    return {"mass": out[0:2].copy(), "sat1": float(out[2]), "p_face": out[3:9].copy()}
 
 
 def lattice():

@@ -385,11 +385,11 @@ void orc_fields(const orc_params *p, const double *ns, const double *gads2,
  *                   Eq. 18's Delta p is the inlet mean minus the outlet mean.
  * rho_scratch: [2][N].
  */
-void orc_observables(const orc_params *p, const double *ns, const double *f,
-                     double *rho_scratch, double *out /*[9]*/) {
-  init_weights();
+/* Observables of given density fields rho[2][N] (Sec. 4): masses, S_1 of
+ * Eq. 19, mean Eq. A.6 pressure of each reservoir face. */
+void orc_observables_rho(const orc_params *p, const double *ns, const double *rho_scratch,
+                         double *out /*[9]*/) {
   const size_t N = n_nodes(p);
-  density_field(p, f, rho_scratch);
   double mass[2] = {0.0, 0.0}, sat_num = 0.0, sat_den = 0.0;
   double psum[6] = {0, 0, 0, 0, 0, 0};
   double pcnt[6] = {0, 0, 0, 0, 0, 0};
@@ -426,4 +426,13 @@ void orc_observables(const orc_params *p, const double *ns, const double *f,
   out[1] = mass[1];
   out[2] = sat_den > 0.0 ? sat_num / sat_den : NAN;
   for (int k = 0; k < 6; ++k) out[3 + k] = pcnt[k] > 0 ? psum[k] / pcnt[k] : NAN;
+}
+
+/* Observables of the current state: the densities of its populations, then
+ * orc_observables_rho. */
+void orc_observables(const orc_params *p, const double *ns, const double *f,
+                     double *rho_scratch, double *out /*[9]*/) {
+  init_weights();
+  density_field(p, f, rho_scratch);
+  orc_observables_rho(p, ns, rho_scratch, out);
 }

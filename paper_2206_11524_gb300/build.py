@@ -33,7 +33,8 @@ NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC",
 
 SOURCES = ["lbm_kernels.cu", "lbm_api.cu", "lbm_noalloc.cu", "lbm_st_f32.cu",
            "lbm_st_f16.cu", "lbm_st_bf16.cu", "lbm_st_f16l.cu", "lbm_st_bf16l.cu"]
-HEADERS = ["lbm_internal.cuh", "lbm_device.cuh", "lbm_storage_impl.cuh", "lbm_validate.h"]
+HEADERS = ["lbm_internal.cuh", "lbm_device.cuh", "lbm_wave.cuh", "lbm_storage_impl.cuh",
+           "lbm_validate.h"]
 
 
 def _nvcc() -> str:

@@ -43,6 +43,10 @@ struct lbm_ctx {
   int single_pass_zc;     // > 0: lbm_step sweeps once, boxes of this many planes
   int wave_cfg;           // > 0: lbm_step is one wavefront launch of this shape
   int wave_lag;           // planes between a plane's density and its collision
+  uint32_t wave_spin;     // polls of one flag before a wavefront wait gives up
+  int64_t wave_hold;      // flag the warp-item launch leaves unpublished (-1)
+  unsigned *fault_host;   // host-mapped word set by a wait that ran out, or NULL
+  bool fault_seen;        // a device fault was reported for the current state
   std::string err;
 };
 
@@ -158,6 +162,43 @@ size_t pop_offset(const lbm_ctx *c, int k, long long x, long long y, long long z
 }
 
 int parity(const lbm_ctx *c) { return (int)(c->t & 1); }
+
+// The fault word after the context's stream has drained: EINTERNAL (with a
+// message) when a bit is set, which also makes lbm_step refuse to advance
+// the state until it is replaced or the word cleared.
+lbm_status check_fault(lbm_ctx *c) {
+  unsigned v = 0;
+  cudaError_t e = cudaMemcpyAsync(&v, c->ws.fault, sizeof v, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "fault word");
+  if (c->fault_host && *(volatile unsigned *)c->fault_host) v |= hmcsc::kFaultWait;
+  if (v == 0) return LBM_OK;
+  c->fault_seen = true;
+  if (v == hmcsc::kFaultWait)
+    return fail(c, LBM_EINTERNAL,
+                "a wavefront wait ran out (fault word 0x%x): the state is undefined; "
+                "load a checkpoint or set a new state", v);
+  return fail(c, LBM_EINTERNAL,
+              "the bounds-checked build recorded an out-of-range access (fault word 0x%x)", v);
+}
+
+// A new state replaces one a wavefront wait may have left undefined: the
+// wait bit goes (out-of-range bits of checked builds stay until cleared).
+lbm_status clear_wait_fault(lbm_ctx *c) {
+  unsigned v = 0;
+  cudaError_t e = cudaMemcpyAsync(&v, c->ws.fault, sizeof v, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e == cudaSuccess && (v & hmcsc::kFaultWait)) {
+    static const unsigned keep_mask = ~hmcsc::kFaultWait;
+    v &= keep_mask;
+    e = cudaMemcpyAsync(c->ws.fault, &v, sizeof v, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  }
+  if (e != cudaSuccess) return cuda_fail(c, e, "fault word");
+  if (c->fault_host) *(volatile unsigned *)c->fault_host = 0u;
+  c->fault_seen = false;
+  return LBM_OK;
+}
 
 // Reservoir face of node (x, y, z) for reservoir set r (higher face wins).
 int reservoir_face(const hmcsc::Reservoirs &r, const lbm_params &p, int x,
@@ -281,6 +322,26 @@ lbm_status lbm_create(const lbm_params *params, void *d_workspace,
   c->single_pass_zc = 0;
   c->wave_cfg = 0;
   c->wave_lag = hmcsc::kWaveLagDefault;
+  c->wave_spin = hmcsc::kWaveSpinDefault;
+  c->wave_hold = -1;
+  c->fault_seen = false;
+  // A host word the kernels can set when a wavefront wait runs out, so that
+  // lbm_step sees it without waiting for the stream (none where mapped host
+  // memory is unavailable: the checks at the synchronising calls remain).
+  c->fault_host = nullptr;
+  {
+    void *h = nullptr, *d = nullptr;
+    if (cudaHostAlloc(&h, 64, cudaHostAllocMapped) == cudaSuccess) {
+      if (cudaHostGetDevicePointer(&d, h, 0) == cudaSuccess) {
+        *(volatile unsigned *)h = 0u;
+        c->fault_host = static_cast<unsigned *>(h);
+        c->ws.fault_host = static_cast<unsigned *>(d);
+      } else {
+        cudaFreeHost(h);
+      }
+    }
+    cudaGetLastError();  // a failed optional allocation is not an error
+  }
   // Zero the whole workspace once so padding lanes hold defined values.
   cudaError_t e = cudaMemsetAsync(d_workspace, 0, need, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
@@ -292,7 +353,11 @@ lbm_status lbm_create(const lbm_params *params, void *d_workspace,
   return LBM_OK;
 }
 
-void lbm_destroy(lbm_ctx *ctx) { delete ctx; }
+void lbm_destroy(lbm_ctx *ctx) {
+  if (!ctx) return;
+  if (ctx->fault_host) cudaFreeHost(ctx->fault_host);
+  delete ctx;
+}
 
 lbm_status lbm_set_geometry_per_component(lbm_ctx *c, const float *ns1,
                                           const float *ns2, const float *gads2) {
@@ -363,6 +428,8 @@ lbm_status lbm_init_equilibrium(lbm_ctx *c, const float *rho_a,
   if (e != cudaSuccess) return cuda_fail(c, e, "init kernel");
   st = sync_stream(c, "init_equilibrium");
   if (st) return st;
+  st = clear_wait_fault(c);
+  if (st) return st;
   memset(&c->sp.res, 0, sizeof c->sp.res);
   c->t = 0;
   c->rho_at = -1;
@@ -420,6 +487,8 @@ lbm_status lbm_set_populations(lbm_ctx *c, const float *f) {
   }
   lbm_status st = sync_stream(c, "set_populations");
   if (st) return st;
+  st = clear_wait_fault(c);
+  if (st) return st;
   memset(&c->sp.res, 0, sizeof c->sp.res);
   c->t = 0;
   c->rho_at = -1;
@@ -445,6 +514,7 @@ lbm_status lbm_get_populations(lbm_ctx *c, float *f) {
   }
   lbm_status st = sync_stream(c, "get_populations");
   if (st) return st;
+  const lbm_status fst = check_fault(c);
   const int nx = c->params.nx, ny = c->params.ny, nz = c->params.nz;
   for (int s = 0; s < 2; ++s)
     for (int i = 0; i < kQ; ++i)
@@ -478,7 +548,7 @@ lbm_status lbm_get_populations(lbm_ctx *c, float *f) {
             }
             f[((size_t)s * kQ + i) * N + n] = v;
           }
-  return LBM_OK;
+  return fst;
 }
 
 lbm_status lbm_set_bc_velocity(lbm_ctx *c, int face, int layers, double rho_a,
@@ -543,10 +613,16 @@ lbm_status lbm_step(lbm_ctx *c, int n_steps) {
   if (n_steps == 0) return LBM_OK;
   if (!c->have_geometry || !c->have_state)
     return fail(c, LBM_ESTATE, "set geometry and state before stepping");
+  if (c->fault_seen || (c->fault_host && *(volatile unsigned *)c->fault_host)) {
+    c->fault_seen = true;
+    return fail(c, LBM_EINTERNAL,
+                "a wavefront wait ran out in an earlier step: the state is undefined; "
+                "load a checkpoint or set a new state");
+  }
   for (int k = 0; k < n_steps; ++k) {
     if (c->wave_cfg > 0) {
       cudaError_t e = hmcsc::launch_wave(c->sp, c->ws, parity(c), c->wave_cfg, c->wave_lag,
-                                         c->stream);
+                                         c->wave_spin, c->wave_hold, c->stream);
       if (e != cudaSuccess) return cuda_fail(c, e, "wavefront kernel");
       c->rho_at = c->t;
       finish_step(c);
@@ -594,6 +670,16 @@ lbm_status lbm_set_wavefront(lbm_ctx *c, int shape, int lag) {
   return LBM_OK;
 }
 
+lbm_status lbm_set_wavefront_limits(lbm_ctx *c, uint32_t spin_limit, int64_t withhold_flag) {
+  if (!c) return LBM_EINVAL;
+  const long long nflags = (long long)c->params.nz * c->params.ny * c->sp.ntx;
+  if (withhold_flag < -1 || withhold_flag >= nflags)
+    return fail(c, LBM_EINVAL, "withheld flag out of range");
+  c->wave_spin = spin_limit ? spin_limit : hmcsc::kWaveSpinDefault;
+  c->wave_hold = withhold_flag;
+  return LBM_OK;
+}
+
 lbm_status lbm_get_wavefront(const lbm_ctx *c, int *shape, int *lag) {
   if (!c) return LBM_EINVAL;
   if (shape) *shape = c->wave_cfg;
@@ -623,7 +709,9 @@ lbm_status lbm_read_fields(lbm_ctx *c, float *rho_a, float *rho_b, float *u,
                         cudaMemcpyDeviceToHost, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "device-to-host copy");
   }
-  return sync_stream(c, "read_fields");
+  lbm_status st = sync_stream(c, "read_fields");
+  if (st) return st;
+  return check_fault(c);
 }
 
 lbm_status lbm_reduce(lbm_ctx *c, lbm_observables *out) {
@@ -644,6 +732,7 @@ lbm_status lbm_reduce(lbm_ctx *c, lbm_observables *out) {
   if (e != cudaSuccess) return cuda_fail(c, e, "device-to-host copy");
   lbm_status st = sync_stream(c, "reduce");
   if (st) return st;
+  const lbm_status fst = check_fault(c);
   out->mass[0] = r[0];
   out->mass[1] = r[1];
   out->sat1 = r[3] > 0.0 ? r[2] / r[3] : NAN;
@@ -659,6 +748,7 @@ lbm_status lbm_reduce(lbm_ctx *c, lbm_observables *out) {
     out->p_face[k] = r[4 + k] / (double)cnt;
   }
   out->nonfinite = (int64_t)r[10];
+  if (fst) return fst;
   if (out->nonfinite > 0)
     return fail(c, LBM_ENAN, "%lld nodes have non-finite densities",
                 (long long)out->nonfinite);
@@ -693,6 +783,7 @@ lbm_status lbm_sync(lbm_ctx *c, double timeout_s) {
     std::this_thread::sleep_for(std::chrono::microseconds(200));
   }
   cudaEventDestroy(ev);
+  if (st == LBM_OK) st = check_fault(c);
   return st;
 }
 
@@ -734,7 +825,9 @@ lbm_status lbm_save(lbm_ctx *c, void *host_buf, size_t bytes) {
                         enc_bytes(c), cudaMemcpyDeviceToHost, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "device-to-host copy");
   }
-  return sync_stream(c, "save");
+  lbm_status st = sync_stream(c, "save");
+  if (st) return st;
+  return check_fault(c);
 }
 
 lbm_status lbm_load(lbm_ctx *c, const void *host_buf, size_t bytes) {
@@ -761,6 +854,8 @@ lbm_status lbm_load(lbm_ctx *c, const void *host_buf, size_t bytes) {
   }
   lbm_status st = sync_stream(c, "load");
   if (st) return st;
+  st = clear_wait_fault(c);
+  if (st) return st;
   c->t = h.t;
   c->sp.res = h.applied;
   c->rho_at = -1;
@@ -772,8 +867,18 @@ lbm_status lbm_load(lbm_ctx *c, const void *host_buf, size_t bytes) {
 
 namespace {
 
+// Do all lattices of a batch use the wavefront step?  Then the batch
+// advances by one persistent launch per step and AA parity over every
+// lattice, in the first context's wavefront shape and lag.
+bool batch_is_wave(lbm_ctx *const *ctxs, int n) {
+  for (int k = 0; k < n; ++k)
+    if (ctxs[k]->wave_cfg <= 0) return false;
+  return true;
+}
+
 lbm_status batch_check(lbm_ctx *const *ctxs, int n) {
   if (!ctxs || n < 1 || n > hmcsc::kBatchMax) return LBM_EINVAL;
+  long long items = 0;
   for (int k = 0; k < n; ++k) {
     if (!ctxs[k]) return LBM_EINVAL;
     if (!ctxs[k]->have_geometry || !ctxs[k]->have_state) return LBM_ESTATE;
@@ -781,7 +886,12 @@ lbm_status batch_check(lbm_ctx *const *ctxs, int n) {
     if ((ctxs[k]->ws.ns2 != nullptr) != (ctxs[0]->ws.ns2 != nullptr)) return LBM_EINVAL;
     for (int j = 0; j < k; ++j)
       if (ctxs[j] == ctxs[k]) return LBM_EINVAL;
+    items += ((long long)ctxs[k]->params.nz + ctxs[0]->wave_lag) * ctxs[k]->sp.ntx *
+             ctxs[k]->params.ny;
   }
+  // the persistent batched launch numbers every row tile of every group
+  if (batch_is_wave(ctxs, n) && items > 4294967295LL)
+    return fail(ctxs[0], LBM_EINVAL, "batch too large for one wavefront launch");
   return LBM_OK;
 }
 
@@ -797,9 +907,39 @@ void advance_one(lbm_ctx *c) {
   c->t += 1;
 }
 
-// Enqueue n_steps steps of every lattice on stream s: per step one batched
-// density pass and one batched fused pass.
+// Enqueue n_steps steps of every lattice on stream s: per step one
+// persistent wavefront launch over all lattices (when every context uses the
+// row-per-warp wavefront step), else one batched density pass and one
+// batched fused pass.
 lbm_status batch_enqueue(lbm_ctx *const *ctxs, int n, int n_steps, cudaStream_t s) {
+  if (batch_is_wave(ctxs, n)) {
+    for (int k = 0; k < n; ++k)
+      if (ctxs[k]->fault_seen || (ctxs[k]->fault_host && *(volatile unsigned *)ctxs[k]->fault_host)) {
+        ctxs[k]->fault_seen = true;
+        return fail(ctxs[k], LBM_EINTERNAL,
+                    "a wavefront wait ran out in an earlier step: the state is undefined");
+      }
+    static thread_local hmcsc::WaveJob job;
+    for (int step = 0; step < n_steps; ++step) {
+      job.n = n;
+      job.cfg = ctxs[0]->wave_cfg;
+      job.lag = ctxs[0]->wave_lag;
+      job.spin_limit = ctxs[0]->wave_spin;
+      job.hold = ctxs[0]->wave_hold;
+      for (int k = 0; k < n; ++k) {
+        job.sp[k] = &ctxs[k]->sp;
+        job.ws[k] = &ctxs[k]->ws;
+        job.parity[k] = (int)(ctxs[k]->t & 1);
+      }
+      cudaError_t e = hmcsc::launch_wave_batch(job, ctxs[0]->sp.storage, s);
+      if (e != cudaSuccess) {
+        for (int k = 0; k < n; ++k) cuda_fail(ctxs[k], e, "batched wavefront kernel");
+        return LBM_ECUDA;
+      }
+      for (int k = 0; k < n; ++k) advance_one(ctxs[k]);
+    }
+    return LBM_OK;
+  }
   static thread_local hmcsc::BatchArgs a;  // ~16 KB: kept off the stack
   for (int step = 0; step < n_steps; ++step) {
     a.n = n;
@@ -946,6 +1086,11 @@ lbm_status lbm_fault_word(lbm_ctx *c, uint32_t *out, int clear) {
   if (e != cudaSuccess) return cuda_fail(c, e, "fault word");
   lbm_status st = sync_stream(c, "fault word");
   if (st) return st;
+  if (c->fault_host && *(volatile unsigned *)c->fault_host) v |= hmcsc::kFaultWait;
+  if (clear) {
+    if (c->fault_host) *(volatile unsigned *)c->fault_host = 0u;
+    c->fault_seen = false;
+  }
   *out = v;
   return LBM_OK;
 }

@@ -347,23 +347,28 @@ struct Relax {
     br36 = br * (1.0f / 36.0f);
     moving = 0.0f;  // sum of B_i over the 18 moving directions
   }
-  // post-collision values of the opposite pair (i, i + 9)
-  __device__ __forceinline__ void pair(int i, const float (&u)[3], const float (&v)[kQ],
-                                       float &out_i, float &out_j) {
-    const int j = i + 9;
+  // post-collision values of the opposite pair (i, i + 9) from their
+  // pre-collision values vi, vj
+  __device__ __forceinline__ void pair_s(int i, const float (&u)[3], float vi, float vj,
+                                         float &out_i, float &out_j) {
     const float cu = cx(i) * u[0] + cy(i) * u[1] + cz(i) * u[2];
     const float bw = wgt(i) == (1.0f / 18.0f) ? br18 : br36;
     const float even = bw * fmaf(4.5f * cu, cu, base);
     const float odd = (3.0f * bw) * cu;
     const float B_i = even + odd, B_j = even - odd;
     moving += B_i + B_j;
-    out_i = fmaf(a, v[i], fmaf(nsx, v[j], B_i));
-    out_j = fmaf(a, v[j], fmaf(nsx, v[i], B_j));
+    out_i = fmaf(a, vi, fmaf(nsx, vj, B_i));
+    out_j = fmaf(a, vj, fmaf(nsx, vi, B_j));
+  }
+  __device__ __forceinline__ void pair(int i, const float (&u)[3], const float (&v)[kQ],
+                                       float &out_i, float &out_j) {
+    pair_s(i, u, v[i], v[i + 9], out_i, out_j);
   }
   // post-collision rest population: B_0 = b rho_s - sum of the moving B_i
-  __device__ __forceinline__ float rest(const float (&v)[kQ]) const {
-    return fmaf(a + nsx, v[0], br - moving);
+  __device__ __forceinline__ float rest_s(float v0) const {
+    return fmaf(a + nsx, v0, br - moving);
   }
+  __device__ __forceinline__ float rest(const float (&v)[kQ]) const { return rest_s(v[0]); }
 };
 
 template <int PARITY, int ST, typename RS, bool CS = false>
@@ -849,13 +854,15 @@ struct WaveShape {
   static constexpr int minb = storage_local(ST) ? c.minb_local : c.minb;
 };
 struct WaveArgs {
-  unsigned items;  // (nz + lag) * tp
-  int tp;          // tiles per plane: ntx * ceil(ny / by)
+  unsigned items;       // (nz + lag) * tp
+  int tp;               // tiles per plane: ntx * ceil(ny / by)
   int lag;
+  unsigned spin_limit;  // polls of one flag before a wait gives up (a few
+                        // seconds at the default with the back-off); the item
+                        // then goes on and the fault word records kFaultWait
+  long long hold;       // a flag the launch leaves unpublished, -1: none
+                        // (tests of the failure path)
 };
-// Polls of one flag before a wait gives up (a few seconds at most with the
-// back-off); the item then goes on and the fault word records kFaultWait.
-constexpr unsigned kWaveSpinLimit = 1u << 22;
 
 // Flags are polled with relaxed loads, served by L2, so polling leaves the
 // SM's L1 alone (an acquire would drop it, and with it the stencil's cached
@@ -875,6 +882,15 @@ __device__ __forceinline__ void st_release(unsigned *ptr, unsigned v) {
   asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(ptr), "r"(v) : "memory");
 }
 
+// A wavefront wait that ran out: the fault word records it (and the mapped
+// host word, when there is one), and wave[3] names the launch, so that the
+// launch's other waits give up at once while later launches wait as usual.
+__device__ __forceinline__ void wave_fault(const Workspace &w, unsigned epoch) {
+  atomicOr(w.fault, kFaultWait);
+  *(volatile unsigned *)&w.wave[3] = epoch;
+  if (w.fault_host) *(volatile unsigned *)w.fault_host = kFaultWait;
+}
+
 // Densities written earlier in the same launch by other blocks, read after
 // their flags (see above), cached in L1 for the stencil.
 struct WaveRho : GlobalRho {
@@ -889,28 +905,24 @@ struct WaveRho : GlobalRho {
   }
 };
 
-template <int PARITY, int ST, bool PC, int CFG>
-__global__ void __launch_bounds__(WaveShape<ST, CFG>::threads, WaveShape<ST, CFG>::minb)
-    k_wave(StepParams p, Workspace w, WaveArgs a) {
+// One wavefront item: ticket k of the launch's lattice (p, w).  buf is the
+// block's two population buffers (this thread's own slots: [b][i][tid]),
+// epoch the lattice's launch epoch, hold a flag left unpublished (-1: none;
+// failure-path tests).  Ends after a block barrier with the tile's densities
+// stored and published and the buffers free.
+template <int PARITY, int ST, bool PC, int BY>
+__device__ __forceinline__ void wave_tile_item(const StepParams &p, const Workspace &w,
+                                               unsigned k, const WaveArgs &a, long long hold,
+                                               typename Codec2<ST>::T2 (*buf)[kQ][kTile * BY],
+                                               unsigned epoch) {
   using C = Codec2<ST>;
   using T2 = typename C::T2;
-  constexpr int BY = WaveShape<ST, CFG>::c.by, NT = kTile * BY;
-  extern __shared__ __align__(16) unsigned char wave_smem[];
-  T2(*buf)[kQ][NT] = reinterpret_cast<T2(*)[kQ][NT]>(wave_smem);  // [0] collision, [1] density
-  __shared__ unsigned s_ticket[2], s_epoch;
   const int tid = threadIdx.y * kTile + threadIdx.x;
   unsigned *ctl = w.wave, *flag = w.wave + kWaveCtlWords;
   const T2 *f = static_cast<const T2 *>(w.f);
   const long long pairs = p.ntiles * kTilePairs, nodes = p.ntiles * kTile;
   const long long nflags = (long long)p.nz * a.tp;
   const int nty = a.tp / p.ntx;
-  if (tid == 0) {
-    s_epoch = *(volatile unsigned *)&ctl[2] + 1u;
-    s_ticket[0] = atomicAdd(&ctl[0], 1u);
-  }
-  __syncthreads();
-  const unsigned epoch = s_epoch;
-  unsigned k = s_ticket[0];
   // populations of node (x, y, z) into buffer b (this thread's own slots)
   auto copy = [&](int x, int y, int z, int b) {
     const Geo g = make_geo(p, x, y, z);
@@ -935,80 +947,110 @@ __global__ void __launch_bounds__(WaveShape<ST, CFG>::threads, WaveShape<ST, CFG
       v2[i] = v.y;
     }
   };
-  int it = 0;
-  while (k < a.items) {
-    it ^= 1;
-    if (tid == 0) s_ticket[it] = atomicAdd(&ctl[0], 1u);  // next item, read at the end
-    const int grp = (int)(k / (unsigned)a.tp), T = (int)(k % (unsigned)a.tp);
-    const int tx = T % p.ntx, ty = T / p.ntx;
-    const int x = tx * kTile + threadIdx.x, y = ty * BY + threadIdx.y;
-    const bool active = x < p.nx && y < p.ny;
-    const int q = grp - a.lag;                   // plane collided, if >= 0
-    const int zd = grp == 0 ? p.nz - 1 : grp - 1;  // plane summed, if grp < nz
-    const bool has_c = q >= 0, has_d = grp < p.nz;
-    const int xlo = tx * kTile, xhi = min(xlo + kTile, p.nx) - 1;
-    const int ylo = ty * BY, yhi = min(ylo + BY, p.ny) - 1;
-    // one commit group per plane: the collision's first
-    if (has_c && active) copy(x, y, q, 0);
-    cp_async_commit();
-    if (has_d && active) copy(x, y, zd, 1);
-    cp_async_commit();
-    // every warp waits for the 27 tiles' densities itself
-    if (has_c && threadIdx.x < 27) {
-      const int l = threadIdx.x;
-      const int dx = l % 3 - 1, dy = (l / 3) % 3 - 1, dz = l / 9 - 1;
-      const int zz = (q + dz + p.nz) % p.nz, yy = (ty + dy + nty) % nty,
-                xx = (tx + dx + p.ntx) % p.ntx;
-      long long fi = (long long)zz * a.tp + (long long)yy * p.ntx + xx;
-      if (kChecked && !in_bounds(w.fault, fi, nflags, kFaultFlag)) fi = 0;
-      // after one wait has run out the others give up at once
-      unsigned n = 0;
-      while (ld_relaxed(&flag[fi]) != epoch) {
-        if (++n == kWaveSpinLimit) {
-          atomicOr(w.fault, kFaultWait);
-          break;
-        }
-        if ((n & 255u) == 0 && (*(volatile unsigned *)w.fault & kFaultWait)) break;
-        __nanosleep(64);
+  const int grp = (int)(k / (unsigned)a.tp), T = (int)(k % (unsigned)a.tp);
+  const int tx = T % p.ntx, ty = T / p.ntx;
+  const int x = tx * kTile + threadIdx.x, y = ty * BY + threadIdx.y;
+  const bool active = x < p.nx && y < p.ny;
+  const int q = grp - a.lag;                     // plane collided, if >= 0
+  const int zd = grp == 0 ? p.nz - 1 : grp - 1;  // plane summed, if grp < nz
+  const bool has_c = q >= 0, has_d = grp < p.nz;
+  const int xlo = tx * kTile, xhi = min(xlo + kTile, p.nx) - 1;
+  const int ylo = ty * BY, yhi = min(ylo + BY, p.ny) - 1;
+  // one commit group per plane: the collision's first
+  if (has_c && active) copy(x, y, q, 0);
+  cp_async_commit();
+  if (has_d && active) copy(x, y, zd, 1);
+  cp_async_commit();
+  // every warp waits for the 27 tiles' densities itself
+  if (has_c && threadIdx.x < 27) {
+    const int l = threadIdx.x;
+    const int dx = l % 3 - 1, dy = (l / 3) % 3 - 1, dz = l / 9 - 1;
+    const int zz = (q + dz + p.nz) % p.nz, yy = (ty + dy + nty) % nty,
+              xx = (tx + dx + p.ntx) % p.ntx;
+    long long fi = (long long)zz * a.tp + (long long)yy * p.ntx + xx;
+    if (kChecked && !in_bounds(w.fault, fi, nflags, kFaultFlag)) fi = 0;
+    // after one wait of this launch has run out the others give up at once
+    unsigned n = 0;
+    while (ld_relaxed(&flag[fi]) != epoch) {
+      if (++n == a.spin_limit) {
+        wave_fault(w, epoch);
+        break;
       }
+      if ((n & 255u) == 0 && *(volatile unsigned *)&ctl[3] == epoch) break;
+      __nanosleep(64);
     }
-    __syncwarp();  // the densities this warp's collisions read are published
-    if (has_c && active) {
-      cp_async_wait<1>();
-      const Geo g = make_geo(p, x, y, q);
-      float f1[kQ], f2[kQ];
-      decode(0, g.node(0, 0, 0), f1, f2);
-      reservoir_state(p, box_in_reservoir(p, xlo, xhi, ylo, yhi, q, q), x, y, q, f1, f2);
-      collide_loaded<PARITY, ST, PC, WaveRho>(p, w, g, WaveRho{global_rho(p, w, g)}, f1, f2);
-    }
-    cp_async_wait<0>();
-    if (has_d && active) {
-      const long long own = ((long long)(zd * p.ny + y) * p.ntx + tx) * kTile + threadIdx.x;
-      float v1[kQ], v2[kQ];
-      decode(1, (int)own, v1, v2);
-      reservoir_state(p, box_in_reservoir(p, xlo, xhi, ylo, yhi, zd, zd), x, y, zd, v1, v2);
-      if (in_bounds(w.fault, own, nodes, kFaultRhoStore))
-        w.rho[own] = make_float2(sum19(v1), sum19(v2));
-    }
-    __syncthreads();  // the tile's densities are stored, the buffers free
-    if (has_d && tid == 0) {
-      long long fi = (long long)zd * a.tp + T;
-      if (!kChecked || in_bounds(w.fault, fi, nflags, kFaultFlag)) st_release(&flag[fi], epoch);
-    }
-    k = s_ticket[it];
   }
-  // The last block out resets the ticket and advances the epoch for the
-  // next launch.
-  if (tid == 0) {
+  __syncwarp();  // the densities this warp's collisions read are published
+  if (has_c && active) {
+    cp_async_wait<1>();
+    const Geo g = make_geo(p, x, y, q);
+    float f1[kQ], f2[kQ];
+    decode(0, g.node(0, 0, 0), f1, f2);
+    reservoir_state(p, box_in_reservoir(p, xlo, xhi, ylo, yhi, q, q), x, y, q, f1, f2);
+    collide_loaded<PARITY, ST, PC, WaveRho>(p, w, g, WaveRho{global_rho(p, w, g)}, f1, f2);
+  }
+  cp_async_wait<0>();
+  if (has_d && active) {
+    const long long own = ((long long)(zd * p.ny + y) * p.ntx + tx) * kTile + threadIdx.x;
+    float v1[kQ], v2[kQ];
+    decode(1, (int)own, v1, v2);
+    reservoir_state(p, box_in_reservoir(p, xlo, xhi, ylo, yhi, zd, zd), x, y, zd, v1, v2);
+    if (in_bounds(w.fault, own, nodes, kFaultRhoStore))
+      w.rho[own] = make_float2(sum19(v1), sum19(v2));
+  }
+  __syncthreads();  // the tile's densities are stored, the buffers free
+  if (has_d && tid == 0) {
+    long long fi = (long long)zd * a.tp + T;
+    if (fi != hold && (!kChecked || in_bounds(w.fault, fi, nflags, kFaultFlag)))
+      st_release(&flag[fi], epoch);
+  }
+}
+
+// The last block out resets the ticket and done counter (in ctl) and
+// advances the epoch of each of the launch's n lattices (ctls[l][2]) for
+// the next launch.
+__device__ __forceinline__ void wave_exit(unsigned *ctl, unsigned *const *ctls, int n) {
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
     __threadfence();
     if (atomicAdd(&ctl[1], 1u) == gridDim.x - 1) {
       volatile unsigned *vc = ctl;
       vc[0] = 0u;
       vc[1] = 0u;
-      vc[2] = epoch;
+      for (int l = 0; l < n; ++l) {
+        volatile unsigned *e = ctls[l];
+        e[2] = e[2] + 1u;
+      }
       __threadfence();
     }
   }
+}
+
+template <int PARITY, int ST, bool PC, int CFG>
+__global__ void __launch_bounds__(WaveShape<ST, CFG>::threads, WaveShape<ST, CFG>::minb)
+    k_wave(StepParams p, Workspace w, WaveArgs a) {
+  using T2 = typename Codec2<ST>::T2;
+  constexpr int BY = WaveShape<ST, CFG>::c.by, NT = kTile * BY;
+  extern __shared__ __align__(16) unsigned char wave_smem[];
+  T2(*buf)[kQ][NT] = reinterpret_cast<T2(*)[kQ][NT]>(wave_smem);  // [0] collision, [1] density
+  __shared__ unsigned s_ticket[2], s_epoch;
+  const int tid = threadIdx.y * kTile + threadIdx.x;
+  unsigned *ctl = w.wave;
+  if (tid == 0) {
+    s_epoch = *(volatile unsigned *)&ctl[2] + 1u;
+    s_ticket[0] = atomicAdd(&ctl[0], 1u);
+  }
+  __syncthreads();
+  const unsigned epoch = s_epoch;
+  unsigned k = s_ticket[0];
+  int it = 0;
+  while (k < a.items) {
+    it ^= 1;
+    if (tid == 0) s_ticket[it] = atomicAdd(&ctl[0], 1u);  // next item, read at the end
+    wave_tile_item<PARITY, ST, PC, BY>(p, w, k, a, a.hold, buf, epoch);
+    k = s_ticket[it];
+  }
+  unsigned *ctls[1] = {ctl};
+  wave_exit(ctl, ctls, 1);
 }
 
 // ---- single-pass step: density and fused pass in one sweep ----

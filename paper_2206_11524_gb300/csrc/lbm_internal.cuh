@@ -200,7 +200,11 @@ struct Workspace {
                      // bounds-checked builds, and of wavefront waits that
                      // ran out in any build (FaultBits)
   unsigned *wave;    // wavefront step: kWaveCtlWords control words (ticket,
-                     // blocks done, epoch), then the tiles' flags
+                     // blocks done, epoch, epoch of a launch whose wait ran
+                     // out), then the tiles' flags
+  unsigned *fault_host;  // host-mapped word that a wavefront wait which ran
+                         // out also sets (read by lbm_step without waiting
+                         // for the stream), or nullptr
 };
 
 // Bounds-checked builds (compiled with -DHMCSC_CHECKED) test the index of
@@ -280,6 +284,24 @@ static_assert(sizeof(BatchArgs) <= 32000, "kernel parameter limit");
 cudaError_t launch_batch_density(const BatchArgs &a, int storage, cudaStream_t s);
 cudaError_t launch_batch_collide(const BatchArgs &a, int storage, cudaStream_t s);
 
+// One batched wavefront step (k_wave_batch, one launch per AA parity
+// present) over n lattices of one storage kind: lattice k's parameters,
+// workspace and AA parity; wavefront shape cfg (1..kWaveConfigs - 1); lag >=
+// kWaveLagMin.  spin_limit bounds the polls of one flag; hold names a flag
+// of lattice 0 that the launch leaves unpublished (-1: none; tests of the
+// failure path).
+struct WaveJob {
+  int n;
+  const StepParams *sp[kBatchMax];
+  const Workspace *ws[kBatchMax];
+  int parity[kBatchMax];
+  int cfg;
+  int lag;
+  unsigned spin_limit;
+  long long hold;
+};
+constexpr unsigned kWaveSpinDefault = 1u << 22;
+
 // Per-storage launchers (one translation unit per storage kind).
 #define HMCSC_DECLARE_STORAGE_LAUNCHERS(SUF)                                   \
   cudaError_t launch_density_##SUF(const StepParams &, const Workspace &, int, \
@@ -293,7 +315,8 @@ cudaError_t launch_batch_collide(const BatchArgs &a, int storage, cudaStream_t s
   cudaError_t launch_single_pass_##SUF(const StepParams &, const Workspace &,  \
                                        int, int, cudaStream_t);                \
   cudaError_t launch_wave_##SUF(const StepParams &, const Workspace &, int,     \
-                                int, int, cudaStream_t);                       \
+                                int, int, unsigned, long long, cudaStream_t);  \
+  cudaError_t launch_wave_batch_##SUF(const WaveJob &, cudaStream_t);         \
   cudaError_t launch_batch_density_##SUF(const BatchArgs &, cudaStream_t);     \
   cudaError_t launch_batch_collide_##SUF(const BatchArgs &, cudaStream_t);
 HMCSC_DECLARE_STORAGE_LAUNCHERS(f32)
@@ -334,7 +357,9 @@ cudaError_t launch_single_pass(const StepParams &p, const Workspace &w, int pari
 // by L2.  cfg in 1 .. kWaveConfigs - 1 (wave_cfg), lag >= kWaveLagMin.
 // Leaves the step's densities in w.rho like launch_density.
 cudaError_t launch_wave(const StepParams &p, const Workspace &w, int parity,
-                        int cfg, int lag, cudaStream_t s);
+                        int cfg, int lag, unsigned spin_limit, long long hold,
+                        cudaStream_t s);
+cudaError_t launch_wave_batch(const WaveJob &job, int storage, cudaStream_t s);
 cudaError_t launch_reduce(const StepParams &p, const Workspace &w,
                           cudaStream_t s);
 

@@ -145,6 +145,7 @@ size_t workspace_bytes(long long nx, long long ny, long long nz, int storage,
     out->ads2 = per_component ? (float *)(base + o_ads2) : nullptr;
     out->fault = (unsigned *)(base + o_fault);
     out->wave = (unsigned *)(base + o_wave);
+    out->fault_host = nullptr;
   }
   return off;
 }
@@ -213,13 +214,24 @@ cudaError_t launch_single_pass(const StepParams &p, const Workspace &w, int pari
 }
 
 cudaError_t launch_wave(const StepParams &p, const Workspace &w, int parity,
-                        int cfg, int lag, cudaStream_t s) {
+                        int cfg, int lag, unsigned spin_limit, long long hold,
+                        cudaStream_t s) {
   switch (p.storage) {
-    case kF16: return launch_wave_f16(p, w, parity, cfg, lag, s);
-    case kBF16: return launch_wave_bf16(p, w, parity, cfg, lag, s);
-    case kF16L: return launch_wave_f16l(p, w, parity, cfg, lag, s);
-    case kBF16L: return launch_wave_bf16l(p, w, parity, cfg, lag, s);
-    default: return launch_wave_f32(p, w, parity, cfg, lag, s);
+    case kF16: return launch_wave_f16(p, w, parity, cfg, lag, spin_limit, hold, s);
+    case kBF16: return launch_wave_bf16(p, w, parity, cfg, lag, spin_limit, hold, s);
+    case kF16L: return launch_wave_f16l(p, w, parity, cfg, lag, spin_limit, hold, s);
+    case kBF16L: return launch_wave_bf16l(p, w, parity, cfg, lag, spin_limit, hold, s);
+    default: return launch_wave_f32(p, w, parity, cfg, lag, spin_limit, hold, s);
+  }
+}
+
+cudaError_t launch_wave_batch(const WaveJob &job, int storage, cudaStream_t s) {
+  switch (storage) {
+    case kF16: return launch_wave_batch_f16(job, s);
+    case kBF16: return launch_wave_batch_bf16(job, s);
+    case kF16L: return launch_wave_batch_f16l(job, s);
+    case kBF16L: return launch_wave_batch_bf16l(job, s);
+    default: return launch_wave_batch_f32(job, s);
   }
 }
 

@@ -148,7 +148,9 @@ extern "C" LBM_API lbm_status lbm_reduce_fields_noalloc(
   a.nx = nx;
   a.ny = ny;
   a.nz = nz;
-  a.G = G;
+  // the pressure uses G rounded to float, as a context holds it, so the
+  // result is the one lbm_reduce gives for the same state
+  a.G = (double)(float)G;
   a.n = N;
   const int ext[3] = {nx, ny, nz};
   for (int k = 0; k < hmcsc::kFaces; ++k) {

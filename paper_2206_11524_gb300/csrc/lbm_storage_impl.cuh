@@ -3,7 +3,7 @@
 // StorageKind) and HMCSC_SUF (the name suffix) defined.
 #include <mutex>
 
-#include "lbm_device.cuh"
+#include "lbm_wave.cuh"
 
 #define HMCSC_CAT2(a, b) a##_##b
 #define HMCSC_CAT(a, b) HMCSC_CAT2(a, b)
@@ -148,7 +148,8 @@ struct WaveOccupancy {
   int dev = -1, per_sm = 0, sms = 0;
 };
 template <int PARITY, bool PC, int CFG>
-cudaError_t wave_launch(const StepParams &p, const Workspace &w, int lag, cudaStream_t s) {
+cudaError_t wave_launch(const StepParams &p, const Workspace &w, int lag, unsigned spin_limit,
+                        long long hold, cudaStream_t s) {
   using T2 = typename Codec2<kST>::T2;
   constexpr int BY = wave_cfg(CFG).by, NT = kTile * BY;
   constexpr int smem = 2 * kQ * NT * (int)sizeof(T2);
@@ -177,6 +178,8 @@ cudaError_t wave_launch(const StepParams &p, const Workspace &w, int lag, cudaSt
   a.tp = p.ntx * ((p.ny + BY - 1) / BY);
   a.lag = lag;
   a.items = (unsigned)((long long)(p.nz + lag) * a.tp);
+  a.spin_limit = spin_limit;
+  a.hold = hold;
   const long long want = (long long)per_sm * sms;
   const unsigned grid = (unsigned)(want < (long long)a.items ? want : (long long)a.items);
   // A cooperative launch: every block is resident while the others run.
@@ -193,24 +196,118 @@ cudaError_t wave_launch(const StepParams &p, const Workspace &w, int lag, cudaSt
   return cudaLaunchKernelEx(&cfg, kern, p, w, a);
 }
 template <int PARITY, int CFG>
-cudaError_t wave_pc(const StepParams &p, const Workspace &w, int lag, cudaStream_t s) {
-  return w.ns2 ? wave_launch<PARITY, true, CFG>(p, w, lag, s)
-               : wave_launch<PARITY, false, CFG>(p, w, lag, s);
+cudaError_t wave_pc(const StepParams &p, const Workspace &w, int lag, unsigned spin,
+                    long long hold, cudaStream_t s) {
+  return w.ns2 ? wave_launch<PARITY, true, CFG>(p, w, lag, spin, hold, s)
+               : wave_launch<PARITY, false, CFG>(p, w, lag, spin, hold, s);
 }
 template <int PARITY>
-cudaError_t wave_any(const StepParams &p, const Workspace &w, int cfg, int lag, cudaStream_t s) {
+cudaError_t wave_any(const StepParams &p, const Workspace &w, int cfg, int lag, unsigned spin,
+                     long long hold, cudaStream_t s) {
   switch (cfg) {
-    case 2: return wave_pc<PARITY, 2>(p, w, lag, s);
-    case 3: return wave_pc<PARITY, 3>(p, w, lag, s);
-    default: return wave_pc<PARITY, 1>(p, w, lag, s);
+    case 2: return wave_pc<PARITY, 2>(p, w, lag, spin, hold, s);
+    case 3: return wave_pc<PARITY, 3>(p, w, lag, spin, hold, s);
+    default: return wave_pc<PARITY, 1>(p, w, lag, spin, hold, s);
   }
 }
 }  // namespace
 
 cudaError_t HMCSC_NAME(launch_wave)(const StepParams &p, const Workspace &w, int parity,
-                                    int cfg, int lag, cudaStream_t s) {
+                                    int cfg, int lag, unsigned spin_limit, long long hold,
+                                    cudaStream_t s) {
   if (lag < kWaveLagMin) return cudaErrorInvalidValue;
-  return parity == 0 ? wave_any<0>(p, w, cfg, lag, s) : wave_any<1>(p, w, cfg, lag, s);
+  return parity == 0 ? wave_any<0>(p, w, cfg, lag, spin_limit, hold, s)
+                     : wave_any<1>(p, w, cfg, lag, spin_limit, hold, s);
+}
+
+namespace {
+// One persistent launch over the job's lattices idx[0..n) (all of AA parity
+// PARITY), tiles of the wavefront shape CFG.
+template <int PARITY, bool PC, int CFG>
+cudaError_t wave_batch_launch(const WaveJob &job, const int *idx, int n, cudaStream_t s) {
+  using T2 = typename Codec2<kST>::T2;
+  constexpr int BY = wave_cfg(CFG).by, NT = kTile * BY;
+  constexpr int smem = 2 * kQ * NT * (int)sizeof(T2);
+  auto kern = k_wave_batch<PARITY, kST, PC, CFG>;
+  static WaveOccupancy occ[16];
+  static std::mutex occ_mu;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 16) return cudaErrorInvalidDevice;
+  std::unique_lock<std::mutex> lock(occ_mu);
+  WaveOccupancy &o = occ[dev];
+  if (o.dev != dev) {
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o.per_sm, kern, NT, smem);
+    if (e == cudaSuccess)
+      e = cudaDeviceGetAttribute(&o.sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    if (o.per_sm < 1) return cudaErrorInvalidConfiguration;
+    o.dev = dev;
+  }
+  const long long want = (long long)o.per_sm * o.sms;
+  lock.unlock();
+  static thread_local WaveBatch b;  // ~23 KB: kept off the stack
+  b.n = n;
+  b.lag = job.lag;
+  b.spin_limit = job.spin_limit;
+  b.hold = idx[0] == 0 ? job.hold : -1;  // the withheld flag belongs to the job's lattice 0
+  unsigned first = 0;
+  for (int k = 0; k < n; ++k) {
+    WaveLattice &L = b.lat[k];
+    L.p = *job.sp[idx[k]];
+    L.w = *job.ws[idx[k]];
+    L.tp = L.p.ntx * ((L.p.ny + BY - 1) / BY);
+    L.first = first;
+    first += (unsigned)((L.p.nz + job.lag) * L.tp);
+  }
+  b.items = first;
+  const unsigned grid = (unsigned)(want < (long long)first ? want : (long long)first);
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(kTile, BY, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, b);
+}
+// Lattices of each parity in one launch each (a step of a batch whose
+// lattices differ in parity is two launches in a row).
+template <bool PC, int CFG>
+cudaError_t wave_batch_parities(const WaveJob &job, cudaStream_t s) {
+  int idx[2][kBatchMax], n[2] = {0, 0};
+  for (int k = 0; k < job.n; ++k) {
+    const int par = job.parity[k] & 1;
+    idx[par][n[par]++] = k;
+  }
+  for (int par = 0; par < 2; ++par) {
+    if (n[par] == 0) continue;
+    const cudaError_t e = par == 0 ? wave_batch_launch<0, PC, CFG>(job, idx[0], n[0], s)
+                                   : wave_batch_launch<1, PC, CFG>(job, idx[1], n[1], s);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+template <int CFG>
+cudaError_t wave_batch_pc(const WaveJob &job, cudaStream_t s) {
+  return job.ws[0]->ns2 != nullptr ? wave_batch_parities<true, CFG>(job, s)
+                                   : wave_batch_parities<false, CFG>(job, s);
+}
+}  // namespace
+
+cudaError_t HMCSC_NAME(launch_wave_batch)(const WaveJob &job, cudaStream_t s) {
+  if (job.n < 1 || job.n > kBatchMax || job.lag < kWaveLagMin) return cudaErrorInvalidValue;
+  switch (job.cfg) {
+    case 2: return wave_batch_pc<2>(job, s);
+    case 3: return wave_batch_pc<3>(job, s);
+    default: return wave_batch_pc<1>(job, s);
+  }
 }
 
 cudaError_t HMCSC_NAME(launch_batch_density)(const BatchArgs &a, cudaStream_t s) {

@@ -39,7 +39,7 @@ ABI_SYMBOLS = (
     "lbm_batch_graph_destroy", "lbm_set_launch_config",
     "lbm_set_geometry_per_component", "lbm_set_bc_velocity", "lbm_set_single_pass",
     "lbm_build_checked", "lbm_fault_word", "lbm_get_launch_config",
-    "lbm_set_wavefront", "lbm_get_wavefront",
+    "lbm_set_wavefront", "lbm_get_wavefront", "lbm_set_wavefront_limits",
 )
 LBM_DENSITY_CONFIGS, LBM_COLLIDE_CONFIGS = 3, 10
 SINGLE_PASS_MAX_NX = 256
@@ -103,6 +103,7 @@ def load(path: str | None = None):
         "lbm_set_single_pass": (ctypes.c_int, [vp, ctypes.c_int]),
         "lbm_set_wavefront": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int]),
         "lbm_get_wavefront": (ctypes.c_int, [vp] + [ctypes.POINTER(ctypes.c_int)] * 2),
+        "lbm_set_wavefront_limits": (ctypes.c_int, [vp, ctypes.c_uint32, ctypes.c_int64]),
         "lbm_build_checked": (ctypes.c_int, []),
         "lbm_get_launch_config": (ctypes.c_int, [vp] + [ctypes.POINTER(ctypes.c_int)] * 3),
         "lbm_fault_word": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_uint32), ctypes.c_int]),
@@ -239,6 +240,11 @@ def lbm_set_single_pass(ctx, planes):
 
 def lbm_set_wavefront(ctx, shape, lag=0):
     return _check(ctx, load().lbm_set_wavefront(ctx, int(shape), int(lag)))
+
+
+def lbm_set_wavefront_limits(ctx, spin_limit=0, withhold_flag=-1):
+    return _check(ctx, load().lbm_set_wavefront_limits(ctx, int(spin_limit),
+                                                        int(withhold_flag)))
 
 
 def lbm_get_wavefront(ctx):
@@ -444,7 +450,8 @@ class Lattice:
     def set_wavefront(self, shape, lag=0):
         """Wavefront lbm_step of tile shape `shape` (1: 32 x 4, 2: 32 x 2,
         3: 32 x 8 nodes; 0: off) with densities `lag` planes ahead (0:
-        default)."""
+        default); lbm_batch_step then also steps such lattices together in
+        one wavefront launch."""
         lbm_set_wavefront(self.ctx, shape, lag)
 
     def wavefront(self):

@@ -2,15 +2,18 @@
 
 Requests (a lattice, its geometry and wettability, G, a step budget) arrive
 over time.  The server keeps every admitted simulation resident in HBM, runs
-all of them together -- one batched density launch and one batched fused
-launch per time step, captured as CUDA graphs of an even number of steps --
+a batch of them together -- by default one persistent wavefront launch per
+time step over every lattice of the batch (row tiles of all lattices taken
+from one ticket), else one batched density launch and one batched fused
+launch per step -- captured as CUDA graphs of an even number of steps,
 admits new requests between ticks as memory and batch slots free up, and
 returns each result (the observables of its final state) as soon as its step
 budget is spent.  Host-side uploads of newly admitted requests overlap with
 the batch running on the GPU.
 
 `run_sequential` is the one-at-a-time baseline on the same arrival trace:
-each request alone, float32 storage, first come first served.
+each request alone, float32 storage, first come first served, with the
+single-lattice step given (the batched wavefront launch by default).
 
 Metrics: time-to-result (arrival -> result on the host) per request, its
 p50 / p99, and aggregate MLUPS = sum(nodes x steps) / makespan.
@@ -110,13 +113,20 @@ def make_requests(n_req=32, seed=2206, L_min=32, L_max=192, steps_min=1000,
     return reqs
 
 
-def _lattice_for(req: Request, storage: str, stream):
+# wavefront shape of the lattices the server and the baseline create
+# (lbm_set_wavefront: tiles of 32 x 2 nodes); batches of such lattices step
+# in one wavefront launch
+WAVE_BATCH = 2
+
+
+def _lattice_for(req: Request, storage: str, stream, wave=WAVE_BATCH):
     lat = lbm.Lattice(req.L, req.L, req.L, tau=req.tau, G=req.G, stream=stream,
                       storage=storage, rho0=(0.5, 0.5))
     lat.set_geometry(req.ns, req.gads2)
     for face, (Lr, a, b) in req.reservoirs.items():
         lat.set_bc(face, Lr, a, b)
     lat.init_equilibrium(req.rho_a, req.rho_b)
+    lat.set_wavefront(wave)
     return lat
 
 
@@ -151,7 +161,7 @@ class Server:
 
     def __init__(self, storage="f16l", tick_steps=400, use_graphs=True,
                  max_batch=lbm.LBM_BATCH_MAX, hbm_budget=None, keep_state=False,
-                 fill_nodes=1 << 23):
+                 fill_nodes=1 << 23, wave=WAVE_BATCH):
         import torch
         self.torch = torch
         self.storage = storage
@@ -163,6 +173,7 @@ class Server:
         self.stream = torch.cuda.Stream()
         self.keep_state = keep_state
         self.fill_nodes = fill_nodes
+        self.wave = wave          # 0: the two batched passes
         self._graphs = {}
         self.ticks = 0
         self.graph_launches = 0
@@ -175,7 +186,7 @@ class Server:
             if used + need > self.budget:
                 break
             pending.pop(0)
-            lat = _lattice_for(req, self.storage, self.torch.cuda.Stream())
+            lat = _lattice_for(req, self.storage, self.torch.cuda.Stream(), self.wave)
             active.append(_Slot(req, lat, req.steps, now))
             used += need
         return used
@@ -269,7 +280,7 @@ class Server:
         return results
 
 
-def run_sequential(requests, storage="f32"):
+def run_sequential(requests, storage="f32", wave=WAVE_BATCH):
     """One request at a time, first come first served, each with lbm_step."""
     import torch
     stream = torch.cuda.Stream()
@@ -281,7 +292,7 @@ def run_sequential(requests, storage="f32"):
         if wait > 0:
             time.sleep(wait)
         admitted = time.perf_counter() - t0
-        lat = _lattice_for(req, storage, stream)
+        lat = _lattice_for(req, storage, stream, wave)
         lat.step(req.steps)
         obs = lat.observables()
         results.append(Result(req.rid, req.arrival, admitted, time.perf_counter() - t0,
@@ -303,33 +314,51 @@ def summarize(results):
 
 
 def compare(n_req=24, L_min=32, L_max=160, steps_min=1000, steps_max=6000,
-            storage="f16l", load=0.9, seed=2206, tick_steps=400):
+            storage="f16l", load=0.9, seed=2206, tick_steps=400, overload=True,
+            wave=WAVE_BATCH):
     """Continuous batching against one-at-a-time float32 runs on the same
     seeded trace, offered at `load` x the sequential capacity (measured on
     three median-size requests of the trace): the arrival times are Poisson
-    at that rate.  Returns both summaries and the trace description."""
+    at that rate.  With `overload`, both arms also run the trace with every
+    request arriving at t = 0, which shows capacity (aggregate MLUPS) rather
+    than the arrival rate.  Returns the summaries and the trace description."""
     reqs = make_requests(n_req=n_req, seed=seed, L_min=L_min, L_max=L_max,
                          steps_min=steps_min, steps_max=steps_max, base_n=L_max)
+    out = {}
+    if overload:
+        for r in reqs:
+            r.arrival = 0.0
+        seq0 = summarize(run_sequential(reqs, wave=wave))
+        srv0 = Server(storage=storage, tick_steps=tick_steps, wave=wave)
+        bat0 = summarize(srv0.run(reqs))
+        bat0.update(storage=storage, graph_launches=srv0.graph_launches,
+                    captures=srv0.captures, ticks=srv0.ticks)
+        seq0.update(storage="f32")
+        out["overload"] = {"batched": bat0, "sequential": seq0,
+                           "arrivals": "all requests at t = 0"}
     work = [r.nodes * r.steps for r in reqs]
     probe = sorted(reqs, key=lambda r: r.nodes)[len(reqs) // 2 - 1: len(reqs) // 2 + 2]
     for r in probe:
         r.arrival = 0.0
-    cal = summarize(run_sequential(probe))
+    cal = summarize(run_sequential(probe, wave=wave))
     rate = load * cal["mlups"] * 1e6 / (sum(work) / len(work))
     rng = np.random.default_rng(seed + 1)
     t = 0.0
     for r in reqs:
         t += float(rng.exponential(1.0 / rate))
         r.arrival = t
-    seq = summarize(run_sequential(reqs))
-    srv = Server(storage=storage, tick_steps=tick_steps)
+    seq = summarize(run_sequential(reqs, wave=wave))
+    srv = Server(storage=storage, tick_steps=tick_steps, wave=wave)
     bat = summarize(srv.run(reqs))
     bat.update(storage=storage, graph_launches=srv.graph_launches,
                captures=srv.captures, ticks=srv.ticks)
     seq.update(storage="f32")
-    return {"trace": f"{len(reqs)} requests, cubic L in [{L_min}, {L_max}] "
-                     f"log-uniform, steps U{{{steps_min}..{steps_max}}}, Poisson "
-                     f"arrivals at {load} x sequential capacity ({rate:.3f}/s), "
-                     "seeded electrode crops with per-request G and binder "
-                     "wettability",
-            "batched": bat, "sequential": seq}
+    out.update({"trace": f"{len(reqs)} requests, cubic L in [{L_min}, {L_max}] "
+                         f"log-uniform, steps U{{{steps_min}..{steps_max}}}, Poisson "
+                         f"arrivals at {load} x sequential capacity ({rate:.3f}/s), "
+                         "seeded electrode crops with per-request G and binder "
+                         "wettability",
+                "step": ("persistent wavefront launch over the batch" if wave
+                         else "two batched passes"),
+                "batched": bat, "sequential": seq})
+    return out

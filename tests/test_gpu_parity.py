@@ -41,14 +41,21 @@ def w64(a):
     return np.asarray(a, dtype=np.float32).astype(np.float64)
 
 
+# The forms lbm_step can take: two passes (density pass, fused pass) and
+# the wavefront launch in its three tile shapes (shape 2 with lag 4 is the
+# one the benchmark times).  Each is compared with the oracle directly.
+FORMS = {"two_pass": (0, 0), "wave_32x2": (2, 4), "wave_32x4": (1, 3), "wave_32x8": (3, 6)}
+
+
 def pair(shape, tau=(0.8, 1.3), G=1.75, F=(2e-5, -1e-5, 3e-5), ns=None,
-         gads=None, res=None):
+         gads=None, res=None, form="two_pass"):
     nz, ny, nx = shape
     if ns is None:
         ns = np.zeros(shape)
     if gads is None:
         gads = np.zeros(shape)
     g = lbm.Lattice(nx, ny, nz, tau=tau, G=G, F_ext=F)
+    g.set_wavefront(*FORMS[form])
     g.set_geometry(ns, gads)
     p = oracle.Params(nx, ny, nz, tau=tuple(float(np.float32(t)) for t in tau),
                       G=float(np.float32(G)),
@@ -80,14 +87,16 @@ def check_fields(g, r, u_mode="relative", tol=1e-5):
 SHAPES = [(5, 4, 7), (3, 9, 33), (2, 5, 64), (1, 1, 1), (1, 2, 3), (4, 1, 1)]
 
 
+@pytest.mark.parametrize("form", sorted(FORMS))
 @pytest.mark.parametrize("shape", SHAPES)
-def test_populations_match_for_three_steps(shape):
+def test_populations_match_for_three_steps(shape, form):
     """Random populations, random n_s (exact 0 and 1 included) and G_ads,
     body force, unequal tau: every population after 1, 2 and 3 steps (both
-    AA parities, read back in natural layout)."""
+    AA parities, read back in natural layout), for every form of the
+    step."""
     seed = sum(shape)
     ns, gads = synth.random_geometry(shape, seed)
-    g, r = pair(shape, ns=ns, gads=gads)
+    g, r = pair(shape, ns=ns, gads=gads, form=form)
     f0 = synth.random_state(shape, seed + 1).astype(np.float32)
     g.set_populations(f0)
     r.set_populations(f0.astype(np.float64))
@@ -99,12 +108,13 @@ def test_populations_match_for_three_steps(shape):
     check_fields(g, r)
 
 
-def test_reservoirs_and_corners_match():
+@pytest.mark.parametrize("form", sorted(FORMS))
+def test_reservoirs_and_corners_match(form):
     """Reservoirs on -x, +x and -y (overlapping corners, higher face wins)."""
     shape = (3, 10, 16)
     ns, gads = synth.random_geometry(shape, 11)
     res = {0: (4, 1.04, 0.01), 1: (3, 0.01, 0.99), 2: (2, 0.5, 0.5)}
-    g, r = pair(shape, ns=ns, gads=gads, res=res)
+    g, r = pair(shape, ns=ns, gads=gads, res=res, form=form)
     ra = np.where(np.arange(16) < 8, 0.99, 0.01) * np.ones(shape)
     g.init_equilibrium(ra, 1.0 - ra)
     r.init_equilibrium(w64(ra), w64(1.0 - ra))
@@ -118,14 +128,15 @@ def test_reservoirs_and_corners_match():
     assert all(math.isnan(v) for v in og["p_face"][3:])
 
 
-def test_inlet_ramp_between_steps():
+@pytest.mark.parametrize("form", ["two_pass", "wave_32x2"])
+def test_inlet_ramp_between_steps(form):
     """An inlet reservoir whose density is raised between steps (the ramp of
     Sec. 4) and a face added mid-run: GPU and oracle apply each change at the
     end of the next step."""
     shape = (4, 6, 20)
     ns, gads = synth.random_geometry(shape, 91)
     res = {0: (4, 1.00, 0.02), 1: (4, 0.02, 0.99)}
-    g, r = pair(shape, ns=ns, gads=gads, res=res)
+    g, r = pair(shape, ns=ns, gads=gads, res=res, form=form)
     ra = np.where(np.arange(20) < 10, 0.99, 0.02) * np.ones(shape)
     g.init_equilibrium(ra, 1.0 - ra)
     r.init_equilibrium(w64(ra), w64(1.0 - ra))
@@ -149,14 +160,15 @@ def test_inlet_ramp_between_steps():
     assert np.array_equal(g.populations(), want)
 
 
-def test_gray_slab_500_steps():
+@pytest.mark.parametrize("form", ["two_pass", "wave_32x2"])
+def test_gray_slab_500_steps(form):
     """The 32 x 16 x 16 gray-slab workload (n_s = 0.5 at x = 12..19, fluid 1
     for x < 16, majority 1.0 / minority 0.03, tau = 1, G = 1.75, F along x)
     for 500 steps: fields within tolerance, per-component mass conserved,
     and a second run bit-identical."""
     case = synth.gray_slab()
     g, r = pair(case.shape, tau=case.tau, G=case.G, F=case.F_ext, ns=case.ns,
-                gads=case.gads2)
+                gads=case.gads2, form=form)
     g.init_equilibrium(case.rho_a, case.rho_b)
     r.init_equilibrium(w64(case.rho_a), w64(case.rho_b))
     m0 = g.observables()["mass"]
@@ -184,6 +196,34 @@ def test_brinkman_variant_force_along_slab():
     uy = fg["u"][1].mean(axis=(0, 1))
     # slower inside the gray slab than in the free fluid
     assert uy[12:20].mean() < uy[:10].mean()
+
+
+def test_saturation_of_a_constructed_state():
+    """S_1 (Eq. 19) of the state built to 37/67 in the oracle pins (the tie
+    rho_1 = 0.5, solid and fractional cells, reservoir layers excluded):
+    the GPU reduction gives the oracle's value on the same float32 inputs."""
+    nx, ny, nz = 10, 2, 2
+    shape = (nz, ny, nx)
+    cols = {0: (1.0, 0.0), 1: (1.0, 0.0), 2: (1.0, 0.0), 3: (0.5, 0.25), 4: (0.7, 1.0),
+            5: (0.4999, 0.5), 6: (0.9, 0.9), 7: (0.1, 0.0), 8: (0.2, 0.3), 9: (0.2, 0.3)}
+    ns = np.zeros(shape, np.float32)
+    f = np.zeros((2, 19) + shape, np.float32)
+    for x, (r1, s_) in cols.items():
+        ns[..., x] = s_
+        f[0, 0, ..., x] = r1
+        f[1, 0, ..., x] = 0.3
+    res = {0: (2, 1.0, 0.01), 1: (2, 0.01, 1.0)}
+    g = lbm.Lattice(nx, ny, nz)
+    g.set_geometry(ns)
+    for face, (L, a, b) in res.items():
+        g.set_bc(face, L, a, b)
+    g.set_populations(f)
+    r = oracle.Sim(oracle.Params(nx, ny, nz, reservoirs=res), w64(ns))
+    r.set_populations(f.astype(np.float64))
+    og, orf = g.observables(), r.observables()
+    assert abs(og["sat1"] - orf["sat1"]) < 1e-12
+    assert abs(og["sat1"] - 37.0 / 67.0) < 1e-6   # float32 n_s of 0.9, 0.25
+    g.close()
 
 
 def test_observables_match():
@@ -348,15 +388,17 @@ def _sampled_reference(case, nodes, steps):
     return np.array(out)
 
 
+@pytest.mark.parametrize("form", sorted(FORMS))
 @pytest.mark.parametrize("steps", [2, 3])
-def test_full_size_electrode_sampled(steps):
-    """The 256^3 synthetic electrode in the benchmark's launch configuration:
-    after 2 (even) and 3 (odd AA parity) steps, the populations of sampled
-    interior nodes equal the oracle's, each computed on a box around the
-    node."""
+def test_full_size_electrode_sampled(steps, form):
+    """The 256^3 synthetic electrode, in every form of the step (the
+    benchmark times the wavefront launch the tuner picks): after 2 (even)
+    and 3 (odd AA parity) steps, the populations of sampled interior nodes
+    equal the oracle's, each computed on a box around the node."""
     case = synth.electrode((256, 256, 256))
     nz, ny, nx = case.shape
     g = lbm.Lattice(nx, ny, nz, tau=case.tau, G=case.G, F_ext=case.F_ext)
+    g.set_wavefront(*FORMS[form])
     g.set_geometry(case.ns, case.gads2)
     for face, (L, r1, r2) in case.reservoirs.items():
         g.set_bc(face, L, r1, r2)
@@ -375,7 +417,8 @@ def test_full_size_electrode_sampled(steps):
     g.close()
 
 
-def test_velocity_boundary_cells_match():
+@pytest.mark.parametrize("form", sorted(FORMS))
+def test_velocity_boundary_cells_match(form):
     """Boundary cells held at a prescribed velocity on two faces (the
     Couette boundaries of Sec. 3.1) plus a density reservoir: populations
     after 1-3 steps and the fields."""
@@ -385,6 +428,7 @@ def test_velocity_boundary_cells_match():
            1: (3, 0.02, 0.99)}
     nz, ny, nx = shape
     g = lbm.Lattice(nx, ny, nz, tau=(0.9, 1.2), G=1.5, F_ext=(1e-5, 0, 0))
+    g.set_wavefront(*FORMS[form])
     g.set_geometry(ns, gads)
     for face, entry in res.items():
         g.set_bc(face, entry[0], entry[1], entry[2],

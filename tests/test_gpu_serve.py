@@ -1,11 +1,14 @@
 """Batched stepping, CUDA graphs and the continuous-batching server: every
-simulation's result is the same alone and in the mix (bit for bit: the
-batched kernels run the same per-node arithmetic)."""
+simulation's result matches the FP64 oracle and is the same alone and in the
+mix (bit for bit: the batched kernels run the same per-node arithmetic), for
+both batched forms: the two batched passes, and the persistent wavefront
+launch over all lattices (contexts on the wavefront step)."""
 import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")
 
+import oracle
 from paper_2206_11524_gb300 import build, lbm, serve, synth
 
 pytestmark = pytest.mark.gpu
@@ -19,7 +22,65 @@ def _built():
     lbm.load()
 
 
-def _lattices(storage, shapes=((20, 12, 40), (8, 30, 64), (17, 9, 33))):
+def _w64(a):
+    return np.asarray(a, dtype=np.float32).astype(np.float64)
+
+
+@pytest.mark.parametrize("wave", [0, 2])
+def test_batch_matches_oracle(wave):
+    """A mixed batch -- three lattice sizes (ragged x-tiles), reservoirs on
+    two of them, unequal tau, a body force, random states and geometry --
+    against the oracle: every population after each batched call, also once
+    the lattices' AA parities differ."""
+    shapes = ((5, 9, 40), (8, 6, 33), (3, 12, 64))
+    res_of = ({0: (2, 1.04, 0.02)}, {}, {1: (3, 0.02, 0.99), 2: (1, 0.5, 0.4)})
+    tau, G, F = (0.9, 1.2), 1.6, (1e-5, -2e-5, 3e-5)
+    gpu, ref = [], []
+    for k, shape in enumerate(shapes):
+        nz, ny, nx = shape
+        ns, gads = synth.random_geometry(shape, 40 + k)
+        f0 = synth.random_state(shape, 50 + k).astype(np.float32)
+        g = lbm.Lattice(nx, ny, nz, tau=tau, G=G, F_ext=F)
+        g.set_geometry(ns, gads)
+        for face, (L, a, b) in res_of[k].items():
+            g.set_bc(face, L, a, b)
+        g.set_populations(f0)
+        g.set_wavefront(wave)
+        p = oracle.Params(nx, ny, nz, tau=tuple(float(np.float32(t)) for t in tau),
+                          G=float(np.float32(G)), Fext=tuple(float(np.float32(v)) for v in F),
+                          reservoirs={f: (L, float(np.float32(a)), float(np.float32(b)))
+                                      for f, (L, a, b) in res_of[k].items()})
+        r = oracle.Sim(p, _w64(ns), _w64(gads))
+        r.set_populations(f0.astype(np.float64))
+        gpu.append(g)
+        ref.append(r)
+    stream = torch.cuda.Stream()
+    torch.cuda.synchronize()
+
+    def check(tag):
+        for g, r in zip(gpu, ref):
+            assert g.t == r.t
+            assert np.abs(g.populations() - r.f).max() <= 2e-6 * np.abs(r.f).max(), (tag, g.t)
+
+    lbm.lbm_batch_step([g.ctx for g in gpu], 1, stream.cuda_stream)
+    stream.synchronize()
+    for r in ref:
+        r.step(1)
+    check("all")
+    gpu[1].step(1)                      # lattice 1 alone: parities differ now
+    ref[1].step(1)
+    torch.cuda.synchronize()
+    lbm.lbm_batch_step([g.ctx for g in gpu], 2, stream.cuda_stream)
+    stream.synchronize()
+    for r in ref:
+        r.step(2)
+    check("mixed parities")
+    for g in gpu:
+        assert lbm.lbm_fault_word(g.ctx) == 0
+        g.close()
+
+
+def _lattices(storage, shapes=((20, 12, 40), (8, 30, 64), (17, 9, 33)), wave=0):
     lats = []
     for k, shape in enumerate(shapes):
         ns, gads = synth.random_geometry(shape, 100 + k)
@@ -30,14 +91,16 @@ def _lattices(storage, shapes=((20, 12, 40), (8, 30, 64), (17, 9, 33))):
         g.set_bc(0, 3, 1.04, 0.01)
         ra = np.where(np.arange(nx) < nx // 2, 0.99, 0.02) * np.ones(shape)
         g.init_equilibrium(ra, 1.01 - ra)
+        g.set_wavefront(wave)
         lats.append(g)
     return lats
 
 
+@pytest.mark.parametrize("wave", [0, 2])
 @pytest.mark.parametrize("storage", ["f32", "f16l"])
-def test_batch_step_equals_single_steps(storage):
+def test_batch_step_equals_single_steps(storage, wave):
     alone = _lattices(storage)
-    mixed = _lattices(storage)
+    mixed = _lattices(storage, wave=wave)
     for g in alone:
         g.step(7)
     stream = torch.cuda.Stream()
@@ -52,9 +115,10 @@ def test_batch_step_equals_single_steps(storage):
         assert np.array_equal(a.populations(), b.populations())
 
 
-def test_graph_replay_equals_steps_and_guards_state():
+@pytest.mark.parametrize("wave", [0, 2])
+def test_graph_replay_equals_steps_and_guards_state(wave):
     alone = _lattices("f32")
-    mixed = _lattices("f32")
+    mixed = _lattices("f32", wave=wave)
     stream = torch.cuda.Stream()
     lbm.lbm_batch_step([g.ctx for g in mixed], 1, stream.cuda_stream)  # reservoirs in force
     stream.synchronize()
@@ -85,13 +149,14 @@ def _alone_state(req, storage):
     return f
 
 
+@pytest.mark.parametrize("wave", [0, 2])
 @pytest.mark.parametrize("storage", ["f32", "f16l"])
-def test_server_results_equal_alone_results(storage):
+def test_server_results_equal_alone_results(storage, wave):
     reqs = serve.make_requests(n_req=5, seed=7, L_min=20, L_max=52, steps_min=20,
                                steps_max=60, base_n=64)
     for k, r in enumerate(reqs):        # staggered arrivals: the mix changes
         r.arrival = 0.05 * k
-    srv = serve.Server(storage=storage, tick_steps=8, keep_state=True)
+    srv = serve.Server(storage=storage, tick_steps=8, keep_state=True, wave=wave)
     results = {r.rid: r for r in srv.run(reqs)}
     assert srv.graph_launches > 0
     for req in reqs:

@@ -463,6 +463,67 @@ def test_reservoir_layers_and_observables():
                        rtol=1e-15)
 
 
+def _saturation_state(nx=10, ny=2, nz=2):
+    """A state whose S_1 (Eq. 19) is known by construction.  Reservoir layers
+    of 2 cells at x = 0, 1 (fluid 1) and x = 8, 9 (fluid 2); the six columns
+    between them carry (rho_1, n_s):
+        x = 2: (1.0,    0.0)   filled, weight 1
+        x = 3: (0.5,    0.25)  exactly at the threshold: filled, weight 0.75
+        x = 4: (0.7,    1.0)   filled but solid: weight 0
+        x = 5: (0.4999, 0.5)   not filled, weight 0.5
+        x = 6: (0.9,    0.9)   filled, weight 0.1
+        x = 7: (0.1,    0.0)   not filled, weight 1
+    so S_1 = (1 + 0.75 + 0.1) / (1 + 0.75 + 0 + 0.5 + 0.1 + 1) = 37 / 67.
+    Each density sits in the rest population alone, so sum_i f_i is exactly
+    the value above."""
+    cols = {0: (1.0, 0.0), 1: (1.0, 0.0), 2: (1.0, 0.0), 3: (0.5, 0.25), 4: (0.7, 1.0),
+            5: (0.4999, 0.5), 6: (0.9, 0.9), 7: (0.1, 0.0), 8: (0.2, 0.3), 9: (0.2, 0.3)}
+    shape = (nz, ny, nx)
+    ns = np.zeros(shape)
+    f = np.zeros((2, 19) + shape)
+    for x, (r1, s_) in cols.items():
+        ns[..., x] = s_
+        f[0, 0, ..., x] = r1
+        f[1, 0, ..., x] = 0.3
+    res = {0: (2, 1.0, 0.01), 1: (2, 0.01, 1.0)}
+    return shape, ns, f, res
+
+
+def test_saturation_of_a_constructed_state():
+    """S_1 of Eq. 19 on a state built to a known value (see
+    _saturation_state): the tie rho_1 = 0.5 counts as filled, each cell is
+    weighted by its fluid fraction 1 - n_s, solid cells and the reservoir
+    layers do not count.  Counting rho_1 > 0.5, weighting by n_s, counting
+    all nodes or the reservoirs all give other values."""
+    shape, ns, f, res = _saturation_state()
+    nz, ny, nx = shape
+    s = oracle.Sim(oracle.Params(nx, ny, nz, reservoirs=res), ns)
+    s.set_populations(f)
+    obs = s.observables()
+    assert abs(obs["sat1"] - 37.0 / 67.0) < 1e-14, obs["sat1"]
+    # the same observables computed from the density fields alone
+    dens = oracle.observables_of_densities(oracle.Params(nx, ny, nz, reservoirs=res), ns,
+                                           f[0].sum(axis=0), f[1].sum(axis=0))
+    assert dens["sat1"] == obs["sat1"] and np.array_equal(dens["mass"], obs["mass"])
+    assert abs(obs["mass"][0] - 4 * (3 * 1.0 + 0.5 + 0.7 + 0.4999 + 0.9 + 0.1 + 0.4)) < 1e-13
+    # Eq. 19 with a fraction per component weights by fluid 1's own: a
+    # different n_s,2 changes nothing
+    ns2 = np.where(ns > 0.5, 0.0, 1.0)
+    s2 = oracle.Sim(oracle.Params(nx, ny, nz, reservoirs=res), np.stack([ns, ns2]))
+    s2.set_populations(f)
+    assert s2.observables()["sat1"] == obs["sat1"]
+    # the same state with every column of fluid 1 below the threshold
+    f_empty = f.copy()
+    f_empty[0, 0] = 0.25
+    s.set_populations(f_empty)
+    assert s.observables()["sat1"] == 0.0
+    # and with the fluid fraction summing to zero (all solid between the
+    # reservoirs) S_1 is undefined
+    s3 = oracle.Sim(oracle.Params(nx, ny, nz, reservoirs=res), np.ones(shape))
+    s3.set_populations(f)
+    assert math.isnan(s3.observables()["sat1"])
+
+
 # --------------------------------------------------------------------------
 # Bounce-back fraction per component, n_s,sigma (Eq. 1, Eq. 4 with
 # s = n_s,sigma, Eq. 7; membranes of Sec. 4, porous obstacles of Sec. 3.5)

@@ -10,7 +10,10 @@ library offers and for ragged and degenerate lattices:
     polled (periodic wrap included);
   - a collision waits only on items of earlier groups when lag >= 3, and a
     greedy run of blocks that take tickets in order finishes (no deadlock),
-    while lag = 2 can wait on a later item."""
+    while lag = 2 can wait on a later item;
+  - several lattices in one launch (items numbered lattice by lattice) keep
+    every wait inside the waiting item's own lattice and on a smaller
+    ticket, and a greedy run of blocks finishes."""
 import pytest
 
 BY_OF_SHAPE = {1: 4, 2: 2, 3: 8}
@@ -134,3 +137,41 @@ def test_lag_two_can_wait_on_a_later_item():
     items, tp, _, _ = schedule(64, 20, 17, 2, 2)
     setter = _flag_group(items, tp)
     assert any(setter[fi] >= it["grp"] for it in items for fi in it["waits"])
+
+
+def _batch_schedule(sizes, by, lag):
+    """Items of several lattices numbered lattice by lattice (the batched
+    launch): each item's lattice, and its waits as (lattice, flag)."""
+    items, first = [], 0
+    for r, (nx, ny, nz) in enumerate(sizes):
+        its, tp, _, _ = schedule(nx, ny, nz, by, lag)
+        for it in its:
+            items.append({"r": r, "grp": it["grp"],
+                          "waits": [(r, f) for f in it["waits"]],
+                          "flag": (r, it["flag"]) if it["flag"] is not None else None})
+        first += len(its)
+    return items
+
+
+@pytest.mark.parametrize("by", [2, 4])
+def test_batched_items_wait_inside_their_lattice(by):
+    sizes = [(40, 9, 5), (7, 4, 3), (64, 20, 6), (33, 1, 2)]
+    items = _batch_schedule(sizes, by, 4)
+    setter = {it["flag"]: k for k, it in enumerate(items) if it["flag"] is not None}
+    for k, it in enumerate(items):
+        for wflag in it["waits"]:
+            assert wflag[0] == it["r"]
+            assert setter[wflag] < k
+    for blocks in (1, 5, 64):
+        done, nxt, holding, finished = set(), 0, [None] * blocks, 0
+        while finished < len(items):
+            progress = False
+            for b in range(blocks):
+                if holding[b] is None and nxt < len(items):
+                    holding[b], nxt, progress = nxt, nxt + 1, True
+                k = holding[b]
+                if k is not None and all(w in done for w in items[k]["waits"]):
+                    if items[k]["flag"] is not None:
+                        done.add(items[k]["flag"])
+                    holding[b], finished, progress = None, finished + 1, True
+            assert progress
