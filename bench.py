@@ -273,13 +273,148 @@ def run_reference(args, world, rank):
 
 
 def serving_leg(args):
-    """Continuous batching (16-bit local storage, batched kernels, CUDA
-    graphs) against one-at-a-time float32 runs on the same seeded trace of
-    heterogeneous requests, offered at 0.9 of the sequential capacity."""
+    """Continuous batching (16-bit storage, one wavefront launch per step over
+    the batch, CUDA graphs) against one-at-a-time float32 runs on the same
+    seeded trace of heterogeneous requests: the config-5 trace shape (cubic
+    L log-uniform in [32, 192]) with step budgets scaled down, offered at 0.9
+    of the sequential capacity and with every request arriving at once."""
     from paper_2206_11524_gb300 import serve
-    return serve.compare(n_req=args.serve_requests, L_min=32, L_max=args.serve_lmax,
-                         steps_min=1000, steps_max=args.serve_steps_max,
-                         storage=args.serve_storage, load=0.9, seed=2206)
+    out = serve.compare(n_req=args.serve_requests, L_min=32, L_max=args.serve_lmax,
+                        steps_min=args.serve_steps_min, steps_max=args.serve_steps_max,
+                        storage=args.serve_storage, load=0.9, seed=2206, overload=True)
+    out["config"] = (f"{args.serve_requests} requests, L in [32, {args.serve_lmax}], steps "
+                     f"U{{{args.serve_steps_min}..{args.serve_steps_max}}} (the 5,000-40,000 "
+                     f"of the full trace scaled by {args.serve_steps_max / 40000:.3g})")
+    return out
+
+
+def _lattice_for(case, storage, stream):
+    from paper_2206_11524_gb300 import lbm
+    nz, ny, nx = case.shape
+    lat = lbm.Lattice(nx, ny, nz, tau=case.tau, G=case.G, F_ext=case.F_ext,
+                      stream=stream, storage=storage, rho0=(0.5, 0.5))
+    lat.set_geometry(case.ns, case.gads2)
+    for face, (L, r1, r2) in case.reservoirs.items():
+        lat.set_bc(face, L, r1, r2)
+    lat.init_equilibrium(case.rho_a, case.rho_b)
+    return lat
+
+
+# launch shapes (density, even, odd) measured fastest per storage; the
+# 16-bit storages keep the two-pass step (their wavefront step is slower)
+DEFAULT_LAUNCH = {"f32": (1, 6, 7), "f16": (0, 6, 8), "bf16": (0, 6, 8),
+                  "f16l": (0, 9, 9), "bf16l": (0, 9, 9)}
+
+
+def _time_two_pass(lat, steps, stream):
+    """Mean ms per step and of the fused pass (CUDA events on the stream)."""
+    import torch
+    from paper_2206_11524_gb300 import lbm
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    torch.cuda.synchronize()
+    for e0, e1, e2 in ev:
+        e0.record(stream)
+        lbm.lbm_density(lat.ctx)
+        e1.record(stream)
+        lbm.lbm_collide_stream(lat.ctx)
+        e2.record(stream)
+    torch.cuda.synchronize()
+    step = sum(a.elapsed_time(c) for a, _, c in ev) / steps
+    fused = sum(b.elapsed_time(c) for _, b, c in ev) / steps
+    return step, fused
+
+
+def storage_record(case, storage, steps, warmup, peak):
+    """Two-pass step of one 16-bit storage on the benchmark lattice: MLUPS and
+    the fused pass's roofline on its own algorithmic bytes."""
+    import torch
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        lat = _lattice_for(case, storage, stream)
+    lat.set_launch_config(*DEFAULT_LAUNCH[storage])
+    lat.step(warmup)
+    step_ms, fused_ms = _time_two_pass(lat, steps, stream)
+    N = case.n_nodes
+    bd, bc = STORAGE_BYTES[storage]
+    obs = lat.observables()
+    lat.close()
+    achieved = bc * N / (fused_ms / 1e3) / 1e9
+    return {"storage": storage, "step": "two passes (density pass, fused pass)",
+            "launch_config": list(DEFAULT_LAUNCH[storage]),
+            "mlups": N / (step_ms / 1e3) / 1e6, "ms_per_step": step_ms,
+            "roofline": {"bound": "hbm", "kernel": "fused pass (k_collide_pipe)",
+                         "algorithmic_bytes_per_node": bc, "achieved": achieved,
+                         "peak": peak, "unit": "GB/s", "frac": achieved / peak},
+            "step_bytes_per_node": bd + bc,
+            "step_frac": (bd + bc) * N / (step_ms / 1e3) / 1e9 / peak,
+            "nonfinite": int(obs["nonfinite"])}
+
+
+def large_domain_record(args, peak):
+    """Config 4: the 512 x 512 x 384 synthetic electrode (~100M nodes) in
+    half-precision offset storage: MLUPS, the fused pass's roofline, the end
+    to end rate through the C ABI with host buffers, and the L-infinity
+    error of the saturation curve S_1(t) against a float32 run."""
+    import numpy as np
+    import torch
+    from paper_2206_11524_gb300 import lbm, synth
+    nx, ny, nz = (int(v) for v in args.large_shape.split(","))
+    t0 = time.perf_counter()
+    case = synth.electrode((nz, ny, nx))
+    gen_s = time.perf_counter() - t0
+    N = case.n_nodes
+    stream = torch.cuda.Stream()
+    curves = {}
+    rec = {"shape": [nx, ny, nz], "nodes": N, "storage": args.large_storage,
+           "generation_s": gen_s}
+    for storage in (args.large_storage, "f32"):
+        with torch.cuda.stream(stream):
+            lat = _lattice_for(case, storage, stream)
+        lat.set_launch_config(*DEFAULT_LAUNCH[storage])
+        curve = []
+        for _ in range(args.large_s1_steps // args.large_s1_every):
+            lat.step(args.large_s1_every)
+            curve.append(lat.observables()["sat1"])
+        curves[storage] = np.array(curve)
+        if storage == args.large_storage:
+            lat.step(args.warmup)
+            step_ms, fused_ms = _time_two_pass(lat, args.large_steps, stream)
+            bd, bc = STORAGE_BYTES[storage]
+            achieved = bc * N / (fused_ms / 1e3) / 1e9
+            rec.update({"mlups": N / (step_ms / 1e3) / 1e6, "ms_per_step": step_ms,
+                        "workspace_gb": lat.workspace.numel() / 1e9,
+                        "roofline": {"bound": "hbm", "kernel": "fused pass (k_collide_pipe)",
+                                     "algorithmic_bytes_per_node": bc,
+                                     "achieved": achieved, "peak": peak, "unit": "GB/s",
+                                     "frac": achieved / peak}})
+            # end to end through the C ABI: host geometry and densities in,
+            # the steps, every field back
+            def pinned(shape):
+                return torch.empty(shape, dtype=torch.float32, pin_memory=True).numpy()
+            h = [pinned(case.shape) for _ in range(4)]
+            for a, v in zip(h, (case.ns, case.gads2, case.rho_a, case.rho_b)):
+                a[...] = v
+            out = [pinned(case.shape) for _ in range(3)] + [pinned((3,) + case.shape)]
+            K = args.large_steps
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            lbm.lbm_set_geometry(lat.ctx, h[0], h[1], N)
+            lbm.lbm_init_equilibrium(lat.ctx, h[2], h[3], N)
+            lbm.lbm_step(lat.ctx, K)
+            lbm.lbm_read_fields(lat.ctx, out[0], out[1], out[3], out[2])
+            e2e_s = time.perf_counter() - t1
+            rec["e2e"] = {"value": N * K / e2e_s / 1e6, "unit": UNIT,
+                          "h2d_bytes_per_step": 4 * 4 * N / K,
+                          "d2h_bytes_per_step": 6 * 4 * N / K}
+        lat.close()
+        del lat
+        torch.cuda.empty_cache()
+    err = float(np.abs(curves[args.large_storage] - curves["f32"]).max())
+    rec["sat1_vs_f32"] = {"linf": err, "steps": args.large_s1_steps,
+                          "every": args.large_s1_every,
+                          "sat1_final_f32": float(curves["f32"][-1])}
+    return rec
 
 
 def run_gpu(args, world, rank, local):
@@ -426,8 +561,20 @@ def run_gpu(args, world, rank, local):
         bytes_launch = bytes_collide * N
         achieved = bytes_collide * N / (ms_collide / 1e3) / 1e9
         traffic_bpn = _profiled_traffic("collide_stream") if storage == "f32" else None
+    ws_gb = lat.workspace.numel() / 1e9
     if rank != 0:
         return 0
+    lat.close()
+    del lat
+    torch.cuda.empty_cache()
+    storages = {}
+    if world == 1 and args.storages:
+        for st in args.storages.split(","):
+            storages[f"storage_{st}"] = storage_record(case, st, args.storage_steps,
+                                                       args.warmup, peak)
+    large = None
+    if world == 1 and args.large_shape:
+        large = large_domain_record(args, peak)
     serving = None
     if world == 1 and args.serve_requests > 0:
         serving = serving_leg(args)
@@ -451,7 +598,7 @@ def run_gpu(args, world, rank, local):
                    "storage": storage,
                    "nodes": N, "global_nodes": N * world,
                    "l2": "inputs larger than L2 (working set "
-                         f"{lat.workspace.numel() / 1e9:.2f} GB)",
+                         f"{ws_gb:.2f} GB)",
                    "parallelism": f"replicas x{world}",
                    "launch_config": launch,
                    "wavefront": ({"shape": wave[0], "lag": wave[1]}
@@ -476,10 +623,11 @@ def run_gpu(args, world, rank, local):
         "gpu_launches": (1 if wave is not None else 3 if single else 2) * K,
         "clocks": clk,
         "cpu_baseline": cpu,
+        "large_domain": large,
         "serving": serving,
     }
+    line.update(storages)
     print(json.dumps(line), flush=True)
-    lat.close()
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
@@ -506,10 +654,20 @@ def main(argv=None):
                     help="time the single-pass step with boxes of about this many planes")
     ap.add_argument("--launch-config", default="",
                     help="density,even,odd launch shapes (skips the autotuner)")
-    ap.add_argument("--serve-requests", type=int, default=24)
-    ap.add_argument("--serve-lmax", type=int, default=160)
-    ap.add_argument("--serve-steps-max", type=int, default=6000)
-    ap.add_argument("--serve-storage", default="f16l")
+    ap.add_argument("--serve-requests", type=int, default=256)
+    ap.add_argument("--serve-lmax", type=int, default=192)
+    ap.add_argument("--serve-steps-min", type=int, default=312)
+    ap.add_argument("--serve-steps-max", type=int, default=2500)
+    ap.add_argument("--serve-storage", default="f16")
+    ap.add_argument("--storages", default="f16,f16l",
+                    help="16-bit storages timed on the same lattice (comma list; '' skips)")
+    ap.add_argument("--storage-steps", type=int, default=40)
+    ap.add_argument("--large-shape", default="512,512,384",
+                    help="nx,ny,nz of the large single-domain record ('' skips)")
+    ap.add_argument("--large-storage", default="f16")
+    ap.add_argument("--large-steps", type=int, default=20)
+    ap.add_argument("--large-s1-steps", type=int, default=400)
+    ap.add_argument("--large-s1-every", type=int, default=50)
     ap.add_argument("--cpu-probe", type=float, default=0.0, help=argparse.SUPPRESS)
     args = ap.parse_args(argv)
     if args.cpu_probe > 0:

@@ -8,6 +8,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <thread>
 #include <vector>
@@ -46,6 +47,7 @@ struct lbm_ctx {
   uint32_t wave_spin;     // polls of one flag before a wavefront wait gives up
   int64_t wave_hold;      // flag the warp-item launch leaves unpublished (-1)
   unsigned *fault_host;   // host-mapped word set by a wait that ran out, or NULL
+  int fault_slot;         // its slot in the process-wide page (-1: none)
   bool fault_seen;        // a device fault was reported for the current state
   std::string err;
 };
@@ -60,6 +62,52 @@ struct lbm_graph {
 };
 
 namespace {
+
+// Host-mapped fault words, one per context, from one pinned page allocated
+// once per process (allocating and freeing pinned memory per context would
+// synchronise the device every time a context is destroyed).
+constexpr int kFaultSlots = 4096;
+std::mutex g_fault_mu;
+unsigned *g_fault_host = nullptr;     // host view of the page
+unsigned *g_fault_dev = nullptr;      // its device view
+bool g_fault_tried = false;
+std::vector<int> g_fault_free;
+
+// A slot's host and device pointers, or false when mapped host memory is
+// unavailable or every slot is taken (the synchronising checks remain).
+bool fault_slot_take(unsigned **host, unsigned **dev, int *slot) {
+  std::lock_guard<std::mutex> lock(g_fault_mu);
+  if (!g_fault_tried) {
+    g_fault_tried = true;
+    void *h = nullptr, *d = nullptr;
+    if (cudaHostAlloc(&h, kFaultSlots * 16 * sizeof(unsigned), cudaHostAllocMapped) ==
+        cudaSuccess) {
+      if (cudaHostGetDevicePointer(&d, h, 0) == cudaSuccess) {
+        memset(h, 0, kFaultSlots * 16 * sizeof(unsigned));
+        g_fault_host = static_cast<unsigned *>(h);
+        g_fault_dev = static_cast<unsigned *>(d);
+        for (int k = kFaultSlots - 1; k >= 0; --k) g_fault_free.push_back(k);
+      } else {
+        cudaFreeHost(h);
+      }
+    }
+    cudaGetLastError();  // a failed optional allocation is not an error
+  }
+  if (!g_fault_host || g_fault_free.empty()) return false;
+  *slot = g_fault_free.back();
+  g_fault_free.pop_back();
+  // one word per 64-byte line, so contexts never share a line
+  *host = g_fault_host + *slot * 16;
+  *dev = g_fault_dev + *slot * 16;
+  *(volatile unsigned *)*host = 0u;
+  return true;
+}
+
+void fault_slot_give(int slot) {
+  if (slot < 0) return;
+  std::lock_guard<std::mutex> lock(g_fault_mu);
+  g_fault_free.push_back(slot);
+}
 
 lbm_status fail(lbm_ctx *c, lbm_status s, const char *fmt, ...) {
   if (c) {
@@ -329,18 +377,15 @@ lbm_status lbm_create(const lbm_params *params, void *d_workspace,
   // lbm_step sees it without waiting for the stream (none where mapped host
   // memory is unavailable: the checks at the synchronising calls remain).
   c->fault_host = nullptr;
+  c->fault_slot = -1;
   {
-    void *h = nullptr, *d = nullptr;
-    if (cudaHostAlloc(&h, 64, cudaHostAllocMapped) == cudaSuccess) {
-      if (cudaHostGetDevicePointer(&d, h, 0) == cudaSuccess) {
-        *(volatile unsigned *)h = 0u;
-        c->fault_host = static_cast<unsigned *>(h);
-        c->ws.fault_host = static_cast<unsigned *>(d);
-      } else {
-        cudaFreeHost(h);
-      }
+    unsigned *h = nullptr, *d = nullptr;
+    int slot = -1;
+    if (fault_slot_take(&h, &d, &slot)) {
+      c->fault_host = h;
+      c->ws.fault_host = d;
+      c->fault_slot = slot;
     }
-    cudaGetLastError();  // a failed optional allocation is not an error
   }
   // Zero the whole workspace once so padding lanes hold defined values.
   cudaError_t e = cudaMemsetAsync(d_workspace, 0, need, c->stream);
@@ -355,7 +400,7 @@ lbm_status lbm_create(const lbm_params *params, void *d_workspace,
 
 void lbm_destroy(lbm_ctx *ctx) {
   if (!ctx) return;
-  if (ctx->fault_host) cudaFreeHost(ctx->fault_host);
+  fault_slot_give(ctx->fault_slot);
   delete ctx;
 }
 

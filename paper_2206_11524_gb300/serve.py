@@ -113,10 +113,13 @@ def make_requests(n_req=32, seed=2206, L_min=32, L_max=192, steps_min=1000,
     return reqs
 
 
-# wavefront shape of the lattices the server and the baseline create
-# (lbm_set_wavefront: tiles of 32 x 2 nodes); batches of such lattices step
-# in one wavefront launch
-WAVE_BATCH = 2
+# Step form of the lattices the server and the baseline create: 0 = two
+# passes (the library's default step).  With a wavefront shape
+# (lbm_set_wavefront) a batch steps in one persistent launch instead; on
+# this trace's lattices (32^3 .. 192^3: few tiles per plane, so the
+# dependency chain between groups leaves most blocks idle) that launch is
+# slower than the two batched passes.
+WAVE_BATCH = 0
 
 
 def _lattice_for(req: Request, storage: str, stream, wave=WAVE_BATCH):
@@ -159,7 +162,7 @@ class Server:
     every resident request each tick (processor sharing, which stretches the
     largest requests' latency by the number of requests beside them)."""
 
-    def __init__(self, storage="f16l", tick_steps=400, use_graphs=True,
+    def __init__(self, storage="f16", tick_steps=400, use_graphs=True,
                  max_batch=lbm.LBM_BATCH_MAX, hbm_budget=None, keep_state=False,
                  fill_nodes=1 << 23, wave=WAVE_BATCH):
         import torch
@@ -171,6 +174,9 @@ class Server:
         free, total = torch.cuda.mem_get_info()
         self.budget = int(hbm_budget if hbm_budget is not None else 0.8 * free)
         self.stream = torch.cuda.Stream()
+        # one stream for the set-up of every admitted lattice (uploads
+        # overlap the batch running on self.stream)
+        self.setup_stream = torch.cuda.Stream()
         self.keep_state = keep_state
         self.fill_nodes = fill_nodes
         self.wave = wave          # 0: the two batched passes
@@ -186,7 +192,7 @@ class Server:
             if used + need > self.budget:
                 break
             pending.pop(0)
-            lat = _lattice_for(req, self.storage, self.torch.cuda.Stream(), self.wave)
+            lat = _lattice_for(req, self.storage, self.setup_stream, self.wave)
             active.append(_Slot(req, lat, req.steps, now))
             used += need
         return used
@@ -314,7 +320,7 @@ def summarize(results):
 
 
 def compare(n_req=24, L_min=32, L_max=160, steps_min=1000, steps_max=6000,
-            storage="f16l", load=0.9, seed=2206, tick_steps=400, overload=True,
+            storage="f16", load=0.9, seed=2206, tick_steps=400, overload=True,
             wave=WAVE_BATCH):
     """Continuous batching against one-at-a-time float32 runs on the same
     seeded trace, offered at `load` x the sequential capacity (measured on
@@ -359,6 +365,6 @@ def compare(n_req=24, L_min=32, L_max=160, steps_min=1000, steps_max=6000,
                          "seeded electrode crops with per-request G and binder "
                          "wettability",
                 "step": ("persistent wavefront launch over the batch" if wave
-                         else "two batched passes"),
+                         else "two batched passes (density, fused) per step"),
                 "batched": bat, "sequential": seq})
     return out

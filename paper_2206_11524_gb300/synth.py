@@ -95,11 +95,23 @@ def random_geometry(shape, seed, gads_max=0.3):
     return ns, gads
 
 
+_OFFSETS = {}
+
+
+def _offsets(r):
+    """Integer offset grids (dz, dy, dx) of the cube [-r, r]^3, built once
+    per radius."""
+    g = _OFFSETS.get(r)
+    if g is None:
+        offs = np.arange(-r, r + 1)
+        g = _OFFSETS[r] = np.meshgrid(offs, offs, offs, indexing="ij")
+    return g
+
+
 def _periodic_ball_indices(center, radius, shape):
     nz, ny, nx = shape
     r = int(math.ceil(radius))
-    offs = np.arange(-r, r + 1)
-    dz, dy, dx = np.meshgrid(offs, offs, offs, indexing="ij")
+    dz, dy, dx = _offsets(r)
     fz = center[0] - math.floor(center[0])
     fy = center[1] - math.floor(center[1])
     fx = center[2] - math.floor(center[2])
@@ -110,12 +122,13 @@ def _periodic_ball_indices(center, radius, shape):
 
 
 def _gaussian_field(shape, sigma, rng):
-    """White noise smoothed by a periodic Gaussian (FFT)."""
+    """White noise smoothed by a periodic Gaussian (real FFT)."""
     noise = rng.standard_normal(shape)
-    k = [np.fft.fftfreq(n) for n in shape]
-    kz, ky, kx = np.meshgrid(*k, indexing="ij")
+    kz = np.fft.fftfreq(shape[0])[:, None, None]
+    ky = np.fft.fftfreq(shape[1])[None, :, None]
+    kx = np.fft.rfftfreq(shape[2])[None, None, :]
     filt = np.exp(-2 * (math.pi * sigma) ** 2 * (kx ** 2 + ky ** 2 + kz ** 2))
-    return np.real(np.fft.ifftn(np.fft.fftn(noise) * filt))
+    return np.fft.irfftn(np.fft.rfftn(noise) * filt, s=shape)
 
 
 def _label_components(mask):
@@ -150,16 +163,19 @@ def electrode(n=(256, 256, 256), seed=2206, solid_fraction=0.60,
         radii = rng.uniform(r_min, r_max, batch)
         for c, r in zip(centers, radii):
             zi, yi, xi = _periodic_ball_indices(c, r, shape)
+            # cells this ball adds (its own index list has no repeats)
+            count += int(np.count_nonzero(~solid[zi, yi, xi]))
             solid[zi, yi, xi] = True
-        count = int(solid.sum())
     # Gray binder: Gaussian random field thresholded inside the pore space.
     field = _gaussian_field(shape, binder_sigma, rng)
     pore = ~solid
     want = binder_fraction * solid.size
     if want > 0 and pore.any():
-        vals = np.sort(field[pore])[::-1]
+        vals = field[pore]
         k = min(int(want), vals.size - 1)
-        binder = pore & (field >= vals[k])
+        # the (k+1)-th largest pore value is the threshold
+        thr = np.partition(vals, vals.size - 1 - k)[vals.size - 1 - k]
+        binder = pore & (field >= thr)
     else:
         binder = np.zeros(shape, bool)
     ns = np.where(solid, 1.0, 0.0)

@@ -8,6 +8,9 @@ variable is set.
 
 Tolerances follow from the storage precision: a stored offset d carries an
 absolute rounding error of at most 2^-11 |d| (half) or 2^-8 |d| (bfloat16).
+The observables' tolerances are about three times the errors measured on a
+GB300 (MEASURED below; the runs are deterministic), so a regression of the
+storage error by a factor of three or more fails.
 """
 import json
 import math
@@ -125,7 +128,22 @@ def test_one_step_parity_on_the_stored_state(storage):
     g.close()
 
 
-STORAGE_TOL = {}  # filled per study below
+# Errors against the FP64 oracle measured on a GB300 (every launch form
+# gives the same bits): relative error of the Eq. 2 permeability, relative
+# error of the droplet's Laplace pressure jump, L-infinity error of the
+# S_1(t) curve of the 48^3 electrode.
+MEASURED = {
+    "permeability": {"f32": 1.67e-3, "f16": 1.67e-3, "bf16": 1.68e-3, "f16l": 1.67e-3,
+                     "bf16l": 8.35e-4},
+    "laplace": {"f32": 4.52e-6, "f16": 0.121, "bf16": 0.603, "f16l": 6.41e-5,
+                "bf16l": 2.16e-3},
+    "sat1": {"f32": 0.0, "f16": 1.13e-3, "bf16": 6.52e-3, "f16l": 4.83e-5, "bf16l": 2.11e-4},
+}
+
+
+def _tol(study, storage, floor=0.0):
+    """Three times the measured error (at least `floor`)."""
+    return max(3.0 * MEASURED[study][storage], floor)
 
 
 def _permeability(storage, ns=0.3, n=16, steps=400):
@@ -149,12 +167,11 @@ def test_permeability_error_by_storage():
     float32 itself carries ~2e-3 (the momentum of populations ~0.05 is
     resolved to ~1e-8 per node)."""
     exact = params.permeability(0.3)
-    for st, tol in (("f32", 5e-3), ("f16", 0.05), ("bf16", 0.5), ("f16l", 5e-3),
-                    ("bf16l", 0.05)):
+    for st in ("f32", "f16", "bf16", "f16l", "bf16l"):
         k = _permeability(st)
         err = abs(k / exact - 1)
         RESULTS[f"permeability_rel_err_{st}"] = err
-        assert err < tol, (st, k, exact)
+        assert err < _tol("permeability", st), (st, k, exact)
 
 
 def _droplet_dp(fields, n, R):
@@ -175,8 +192,7 @@ def test_laplace_pressure_jump_by_storage():
     r.init_equilibrium(w64(case.rho_a), w64(case.rho_b))
     r.step(steps)
     dp_ref = _droplet_dp(r.fields(), n, R)
-    for st, tol in (("f32", 1e-4), ("f16", 0.5), ("bf16", 2.0), ("f16l", 2e-2),
-                    ("bf16l", 0.2)):
+    for st in ("f32", "f16", "bf16", "f16l", "bf16l"):
         g = lbm.Lattice(n, n, n, tau=(1.0, 1.0), G=1.75, storage=st, rho0=(0.5, 0.5))
         g.set_geometry(case.ns, case.gads2)
         g.init_equilibrium(case.rho_a, case.rho_b)
@@ -185,7 +201,7 @@ def test_laplace_pressure_jump_by_storage():
         g.close()
         err = abs(dp / dp_ref - 1)
         RESULTS[f"laplace_dp_rel_err_{st}"] = err
-        assert err < tol, (st, dp, dp_ref)
+        assert err < _tol("laplace", st), (st, dp, dp_ref)
     RESULTS["laplace_dp_oracle"] = dp_ref
 
 
@@ -203,8 +219,13 @@ def test_saturation_curve_by_storage():
         r.step(every)
         ref.append(r.observables()["sat1"])
     ref = np.array(ref)
-    for st, tol in (("f32", 2e-3), ("f16", 2e-2), ("bf16", 0.15), ("f16l", 2e-2),
-                    ("bf16l", 0.15)):
+    # float32 (measured: no difference) may put a couple of nodes within
+    # float32 rounding of rho_1 = 0.5 on the other side: two nodes' weight
+    inner = np.zeros(case.shape, bool)
+    inner[..., 4:n - 4] = True
+    two_nodes = 2.0 / float((1.0 - w64(case.ns))[inner].sum())
+    for st in ("f32", "f16", "bf16", "f16l", "bf16l"):
+        tol = _tol("sat1", st, floor=two_nodes)
         g = lbm.Lattice(n, n, n, tau=case.tau, G=case.G, storage=st, rho0=(0.5, 0.5))
         g.set_geometry(case.ns, case.gads2)
         for face, (L, a, b) in case.reservoirs.items():
