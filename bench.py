@@ -273,10 +273,11 @@ def run_reference(args, world, rank):
 
 
 def serving_leg(args):
-    """Continuous batching (16-bit storage, one wavefront launch per step over
-    the batch, CUDA graphs) against one-at-a-time float32 runs on the same
-    seeded trace of heterogeneous requests: the config-5 trace shape (cubic
-    L log-uniform in [32, 192]) with step budgets scaled down, offered at 0.9
+    """Continuous batching (half-offset storage, the two batched passes per
+    step over the batch, CUDA graphs) against one-at-a-time float32 runs
+    (two passes each) on the same seeded trace of heterogeneous requests:
+    the trace shape of the serving workload (cubic L log-uniform in [32,
+    192]) with fewer requests and step budgets scaled down, offered at 0.9
     of the sequential capacity and with every request arriving at once."""
     from paper_2206_11524_gb300 import serve
     out = serve.compare(n_req=args.serve_requests, L_min=32, L_max=args.serve_lmax,
@@ -654,7 +655,7 @@ def main(argv=None):
                     help="time the single-pass step with boxes of about this many planes")
     ap.add_argument("--launch-config", default="",
                     help="density,even,odd launch shapes (skips the autotuner)")
-    ap.add_argument("--serve-requests", type=int, default=256)
+    ap.add_argument("--serve-requests", type=int, default=64)
     ap.add_argument("--serve-lmax", type=int, default=192)
     ap.add_argument("--serve-steps-min", type=int, default=312)
     ap.add_argument("--serve-steps-max", type=int, default=2500)

@@ -301,6 +301,9 @@ struct WaveJob {
   long long hold;
 };
 constexpr unsigned kWaveSpinDefault = 1u << 22;
+// Share of L2 that the planes in flight of one set of a batched wavefront
+// launch may fill (lattices beyond it go to the next set).
+constexpr double kWaveSetL2Share = 0.5;
 
 // Per-storage launchers (one translation unit per storage kind).
 #define HMCSC_DECLARE_STORAGE_LAUNCHERS(SUF)                                   \

@@ -145,7 +145,7 @@ namespace {
 // Resident blocks per SM and SM count of the current device for one k_wave
 // instance (the grid is one wave of persistent blocks).
 struct WaveOccupancy {
-  int dev = -1, per_sm = 0, sms = 0;
+  int dev = -1, per_sm = 0, sms = 0, l2 = 0;
 };
 template <int PARITY, bool PC, int CFG>
 cudaError_t wave_launch(const StepParams &p, const Workspace &w, int lag, unsigned spin_limit,
@@ -243,27 +243,74 @@ cudaError_t wave_batch_launch(const WaveJob &job, const int *idx, int n, cudaStr
       e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o.per_sm, kern, NT, smem);
     if (e == cudaSuccess)
       e = cudaDeviceGetAttribute(&o.sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&o.l2, cudaDevAttrL2CacheSize, dev);
     if (e != cudaSuccess) return e;
     if (o.per_sm < 1) return cudaErrorInvalidConfiguration;
     o.dev = dev;
   }
   const long long want = (long long)o.per_sm * o.sms;
+  // a set's planes in flight may fill this much of L2
+  const double set_budget = kWaveSetL2Share * o.l2;
   lock.unlock();
-  static thread_local WaveBatch b;  // ~23 KB: kept off the stack
+  static thread_local WaveBatch b;  // ~24 KB: kept off the stack
+  // lattices by group count, most first (stable: equal counts keep the
+  // job's order)
+  int ord[kBatchMax];
+  for (int k = 0; k < n; ++k) {
+    int j = k;
+    while (j > 0 && job.sp[idx[ord[j - 1]]]->nz < job.sp[idx[k]]->nz) {
+      ord[j] = ord[j - 1];
+      --j;
+    }
+    ord[j] = k;
+  }
   b.n = n;
   b.lag = job.lag;
   b.spin_limit = job.spin_limit;
-  b.hold = idx[0] == 0 ? job.hold : -1;  // the withheld flag belongs to the job's lattice 0
-  unsigned first = 0;
+  b.hold_lat = -1;
+  b.hold = job.hold;
+  b.tsum[0] = 0;
   for (int k = 0; k < n; ++k) {
     WaveLattice &L = b.lat[k];
-    L.p = *job.sp[idx[k]];
-    L.w = *job.ws[idx[k]];
+    L.p = *job.sp[idx[ord[k]]];
+    L.w = *job.ws[idx[ord[k]]];
     L.tp = L.p.ntx * ((L.p.ny + BY - 1) / BY);
-    L.first = first;
-    first += (unsigned)((L.p.nz + job.lag) * L.tp);
+    b.tsum[k + 1] = b.tsum[k] + (unsigned)L.tp;
+    if (idx[ord[k]] == 0) b.hold_lat = k;  // the withheld flag is the job's lattice 0's
   }
-  b.items = first;
+  // sets: runs of the order whose planes in flight fit the budget together
+  // (a lattice alone may exceed it); segments inside a set: groups
+  // [G_m, G_(m-1)) hold the set's lattices 0 .. m - 1
+  unsigned long long first = 0;
+  int nseg = 0;
+  for (int lb = 0; lb < n;) {
+    double bytes = 0.0;
+    int le = lb;
+    while (le < n) {
+      const WaveLattice &L = b.lat[le];
+      const double lat_bytes =
+          (double)(job.lag + 2) * L.p.ntx * kTile * L.p.ny * kQ * (double)sizeof(T2);
+      if (le > lb && bytes + lat_bytes > set_budget) break;
+      bytes += lat_bytes;
+      ++le;
+    }
+    int g0 = 0;
+    for (int m = le - lb; m >= 1; --m) {
+      const int gend = b.lat[lb + m - 1].p.nz + job.lag;
+      if (gend <= g0) continue;
+      b.seg_first[nseg] = (unsigned)first;
+      b.seg_g0[nseg] = g0;
+      b.seg_lb[nseg] = lb;
+      b.seg_m[nseg] = m;
+      first += (unsigned long long)(gend - g0) * (b.tsum[lb + m] - b.tsum[lb]);
+      g0 = gend;
+      ++nseg;
+    }
+    lb = le;
+  }
+  if (first > 0xFFFFFFFFull) return cudaErrorInvalidValue;  // the host checks this first
+  b.nseg = nseg;
+  b.items = (unsigned)first;
   const unsigned grid = (unsigned)(want < (long long)first ? want : (long long)first);
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;

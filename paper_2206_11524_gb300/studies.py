@@ -13,6 +13,10 @@
 `washburn`    capillary imbibition into a homogeneous gray medium (Sec. 3.4,
               Eq. 16, Table 3): the front position against time for the
               paper's G_ads and n_s series, fitted as x = A sqrt(B t).
+`buckley_leverett`  waterflooding of a homogeneous gray medium (SI,
+              Buckley-Leverett experiment): saturation profiles and front
+              displacement against the Buckley-Leverett solution with
+              k_r = S^a and (1 - S)^a for the paper's bounds a = 1.01, 1.3.
 `serving`     a stream of independent imbibition requests of different
               sizes, microstructures and wettabilities: continuous batching
               in 16-bit storage against one-at-a-time float32 runs (p50 / p99
@@ -250,6 +254,135 @@ def washburn(gads_values=(0.05, 0.10, 0.15, 0.20, 0.25, 0.30, 0.35, 0.40),
     return out
 
 
+# ---- Buckley-Leverett waterflooding (SI) ----
+#
+# Set-up as read from the text (whose axes are garbled: it drives the flow
+# with a body force along the periodic axis while the inlet and outlet sit
+# at the ends of the other): displacement along x through H lu, the body
+# force 1e-4 along x, fluid 1 held at the inlet layers x = 0..3 and fluid 2
+# at the outlet layers, every cell (reservoir layers included) with the same
+# n_s and G_ads = 0, the domain W lu wide and periodic across y.  The
+# reservoirs hold the flat-interface coexistence densities at G = 1.75, so
+# the fluids enter as the bulk phases they are in the medium.  Saturation of
+# fluid 1 is rho_1 normalised between those densities; with both fluids
+# carried in full by every homogenized cell the porosity of the mass balance
+# is 1, and the flux q of the Buckley-Leverett equation is the mean x
+# velocity of Eq. 7 over the medium.
+
+
+def bl_fractional_flow(S, a):
+    """f(S) = (1 + k_r2 / k_r1)^-1 with k_r1 = S^a, k_r2 = (1 - S)^a."""
+    S = np.asarray(S, dtype=np.float64)
+    return S ** a / (S ** a + (1.0 - S) ** a)
+
+
+def bl_dfds(S, a):
+    """df/dS of bl_fractional_flow."""
+    S = np.asarray(S, dtype=np.float64)
+    d = S ** a + (1.0 - S) ** a
+    return a * S ** (a - 1) * (1.0 - S) ** (a - 1) / d ** 2
+
+
+def bl_welge(a):
+    """Shock saturation S_f and shock speed factor f(S_f)/S_f of Welge's
+    tangent from the initial state S = 0: the S where f(S)/S = f'(S)
+    (bisection; S f' - f is positive near 0 and -1 at S = 1 for a > 1)."""
+    lo, hi = 1e-9, 1.0 - 1e-12
+    g = lambda S: float(S * bl_dfds(S, a) - bl_fractional_flow(S, a))
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if g(mid) > 0:
+            lo = mid
+        else:
+            hi = mid
+    Sf = 0.5 * (lo + hi)
+    return Sf, float(bl_fractional_flow(Sf, a)) / Sf
+
+
+def bl_profile(x, Q, a, phi=1.0):
+    """Buckley-Leverett saturation at distance x from the inlet after an
+    injected volume Q per unit area: S travels at (Q / phi) f'(S) for S in
+    [S_f, 1] (f' falls monotonically there), S = 0 ahead of the shock at
+    (Q / phi) f(S_f) / S_f."""
+    Sf, speed = bl_welge(a)
+    S = np.linspace(Sf, 1.0, 20001)
+    xs = (Q / phi) * bl_dfds(S, a)          # decreasing in S
+    x = np.asarray(x, dtype=np.float64)
+    out = np.interp(x, xs[::-1], S[::-1])   # 1 behind the slowest, S_f at the shock
+    return np.where(x >= (Q / phi) * speed, 0.0, out)
+
+
+def bl_setup(ns, H=100, W=5, F=1e-4, storage="f32"):
+    hi, lo = COEXIST_175
+    x = np.arange(H)
+    lat = lbm.Lattice(H, W, 1, tau=(1.0, 1.0), G=1.75, F_ext=(F, 0, 0), storage=storage,
+                      rho0=(0.5, 0.5))
+    lat.set_geometry(np.full((1, W, H), ns))
+    lat.set_bc(0, 4, hi, lo)
+    lat.set_bc(1, 4, lo, hi)
+    ra = np.broadcast_to(np.where(x < 4, hi, lo), (1, W, H)).astype(np.float64)
+    lat.init_equilibrium(ra, hi + lo - ra)
+    return lat
+
+
+def bl_saturation(rho1):
+    hi, lo = COEXIST_175
+    return (np.asarray(rho1, dtype=np.float64) - lo) / (hi - lo)
+
+
+def bl_front(S, x0=4):
+    """Where S falls through 0.5 behind the inlet (linear interpolation),
+    as an x coordinate; x0 before the front enters."""
+    for k in range(x0, len(S) - 1):
+        if S[k] >= 0.5 > S[k + 1]:
+            return k + (S[k] - 0.5) / (S[k] - S[k + 1])
+    return float(x0)
+
+
+def bl_run(ns, H=100, W=5, steps=200000, samples=40, storage="f32"):
+    """Sample times, front positions, injected volume Q(t) (trapezoid over
+    the samples of the mean velocity of the medium) and the last profile
+    S(x) (mean over y)."""
+    lat = bl_setup(ns, H, W, storage=storage)
+    ts, fronts, Q = [0], [4.0], [0.0]
+    q_prev = 0.0
+    for _ in range(samples):
+        lat.step(steps // samples)
+        fl = lat.fields()
+        S = bl_saturation(fl["rho_a"][0].mean(axis=0))
+        q = float(fl["u"][0][0][:, 4:H - 4].astype(np.float64).mean())
+        Q.append(Q[-1] + 0.5 * (q + q_prev) * (lat.t - ts[-1]))
+        q_prev = q
+        ts.append(lat.t)
+        fronts.append(bl_front(S))
+    lat.close()
+    return np.array(ts, float), np.array(fronts), np.array(Q), S
+
+
+def buckley_leverett(ns_values=(0.1, 0.5, 0.9), H=100, W=5, steps=200000, samples=40,
+                     bounds=(1.01, 1.3)):
+    """Per n_s: the front displacement over the last four fifths of the run,
+    the injected volume in that time and their ratio (the shock speed factor
+    f(S_f)/S_f of the Buckley-Leverett solution, to be compared with the
+    bounds'), and the final profile against the two bounds' profiles at the
+    measured injected volume (the inlet face at x = 4)."""
+    out = {"study": "buckley_leverett", "H": H, "W": W, "steps": steps,
+           "bounds": {str(a): dict(zip(("S_f", "speed"), bl_welge(a))) for a in bounds},
+           "runs": []}
+    for ns in ns_values:
+        ts, fr, Q, S = bl_run(ns, H, W, steps, samples)
+        k0 = samples // 5
+        dQ = float(Q[-1] - Q[k0])
+        ratio = float((fr[-1] - fr[k0]) / dQ) if dQ > 0 else float("nan")
+        x = np.arange(H) - 4.0
+        prof = {str(a): bl_profile(x, float(Q[-1]), a).tolist() for a in bounds}
+        out["runs"].append({"ns": ns, "front": float(fr[-1]), "Q": float(Q[-1]),
+                            "shift": float(fr[-1] - fr[k0]), "dQ": dQ,
+                            "speed_ratio": ratio, "profile": S.tolist(),
+                            "bound_profiles": prof})
+    return out
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     sub = ap.add_subparsers(dest="study", required=True)
@@ -272,13 +405,16 @@ def main(argv=None):
     d.add_argument("--n", type=int, default=50)
     d.add_argument("--steps", type=int, default=3000)
     d.add_argument("--out", default="")
+    f = sub.add_parser("buckley_leverett")
+    f.add_argument("--steps", type=int, default=200000)
+    f.add_argument("--out", default="")
     c = sub.add_parser("serving")
     c.add_argument("--requests", type=int, default=256)
     c.add_argument("--lmin", type=int, default=32)
     c.add_argument("--lmax", type=int, default=192)
     c.add_argument("--steps-min", type=int, default=5000)
     c.add_argument("--steps-max", type=int, default=40000)
-    c.add_argument("--storage", default="f16l")
+    c.add_argument("--storage", default="f16")
     c.add_argument("--load", type=float, default=0.9)
     c.add_argument("--out", default="")
     args = ap.parse_args(argv)
@@ -293,6 +429,8 @@ def main(argv=None):
         res = washburn(steps=args.steps)
     elif args.study == "relperm":
         res = relperm(n=args.n, steps=args.steps)
+    elif args.study == "buckley_leverett":
+        res = buckley_leverett(steps=args.steps)
     elif args.study == "saturation":
         res = saturation(shape=tuple(int(v) for v in args.shape.split(",")),
                          storages=tuple(args.storages.split(",")),
@@ -307,7 +445,7 @@ def main(argv=None):
     if args.out:
         with open(args.out, "w") as fh:
             fh.write(text)
-    summary = {k: v for k, v in res.items() if k not in ("rows", "curves")}
+    summary = {k: v for k, v in res.items() if k not in ("rows", "curves", "runs")}
     print(json.dumps(summary))
     return 0
 

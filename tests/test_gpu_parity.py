@@ -529,3 +529,41 @@ def test_washburn_front_matches_oracle_and_table3():
         ts, xs = studies.washburn_front(gads, 0.5, H, 50000)
         a = float((xs ** 2) @ ts / (ts @ ts))
         assert abs(math.sqrt(a / 0.0481) / A_tab - 1) < 0.10, gads
+
+
+def test_buckley_leverett_matches_oracle_and_bounds():
+    """Waterflooding (SI; set-up as read in studies.bl_setup, 100 x 5 lu):
+    the GPU's saturation profile equals the oracle's (one row: the y extent
+    is periodic and the state uniform in y) to 2e-3 and its front to 0.05 lu
+    over 20,000 steps at n_s = 0.1; over the paper's 200,000 steps the
+    front's displacement lies between the injected volume times the shock
+    speed factors of the bounds a = 1.01 and 1.3, give or take 0.5 lu
+    (n_s = 0.1, 0.5), and the saturation behind it between the two bounds'
+    profiles."""
+    from paper_2206_11524_gb300 import studies
+    hi, lo = (float(np.float32(v)) for v in studies.COEXIST_175)
+    H, steps = 100, 20000
+    ts, fr_g, Q_g, S_g = studies.bl_run(0.1, H, 5, steps, samples=4)
+    res = {0: (4, hi, lo), 1: (4, lo, hi)}
+    r = oracle.Sim(oracle.Params(H, 1, 1, tau=(1.0, 1.0), G=1.75,
+                                 Fext=(float(np.float32(1e-4)), 0, 0), reservoirs=res),
+                   w64(np.full((1, 1, H), 0.1)))
+    x = np.arange(H)
+    ra = np.where(x < 4, hi, lo)[None, None] * 1.0
+    r.init_equilibrium(ra, hi + lo - ra)
+    for k in range(4):
+        r.step(steps // 4)
+        S_r = studies.bl_saturation(r.fields()["rho_a"][0, 0])
+        assert abs(fr_g[k + 1] - studies.bl_front(S_r)) < 0.05, (k, fr_g[k + 1])
+    assert np.abs(S_g - S_r).max() < 2e-3
+    out = studies.buckley_leverett(ns_values=(0.1, 0.5), H=H, W=5, steps=200000, samples=40)
+    lo_b = out["bounds"]["1.01"]["speed"]
+    hi_b = out["bounds"]["1.3"]["speed"]
+    for run in out["runs"]:
+        assert lo_b * run["dQ"] - 0.5 < run["shift"] < hi_b * run["dQ"] + 0.5, \
+            (run["ns"], run["shift"], run["dQ"])
+        S = np.array(run["profile"])
+        low = np.array(run["bound_profiles"]["1.3"])
+        behind = (x >= 4) & (x < run["front"] - 3)
+        assert behind.sum() >= 2
+        assert np.all(S[behind] >= low[behind] - 0.02) and np.all(S[behind] <= 1.005)

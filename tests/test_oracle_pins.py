@@ -756,3 +756,91 @@ def test_washburn_fronts_follow_table3():
         B = a / A_tab[0.2] ** 2
         assert r2 > 0.97, (ns, r2)
         assert abs(B / B_tab[ns] - 1) < tol, (ns, B, B_tab[ns])
+
+
+# --------------------------------------------------------------------------
+# Buckley-Leverett waterflooding (SI: Buckley-Leverett experiment)
+# --------------------------------------------------------------------------
+
+def test_buckley_leverett_solution_closed_forms():
+    """The analytic side the oracle is held to: Welge's tangent from S = 0
+    for k_r = S^2, (1 - S)^2 touches f at S_f = 1/sqrt(2) with speed factor
+    (1 + sqrt(2))/2 (f(S)/S = f'(S) solved by hand); the solution conserves
+    the injected volume (integral of S over x equals Q at porosity 1, the
+    Welge balance); and the paper's bounds a = 1.01 and 1.3 give shocks of
+    speed factor just above 1 and about 1.08, a=1.01 the faster-filling."""
+    from paper_2206_11524_gb300 import studies
+    Sf, sp = studies.bl_welge(2.0)
+    assert abs(Sf - 1 / math.sqrt(2)) < 1e-12
+    assert abs(sp - (1 + math.sqrt(2)) / 2) < 1e-12
+    for a in (1.01, 1.3, 2.0):
+        Sf, sp = studies.bl_welge(a)
+        assert abs(studies.bl_dfds(Sf, a) - sp) < 1e-9        # tangent
+        x = np.linspace(0, 60, 600001)
+        S = studies.bl_profile(x, 40.0, a)
+        vol = float(np.sum(0.5 * (S[1:] + S[:-1])) * (x[1] - x[0]))
+        assert abs(vol / 40.0 - 1) < 2e-3, (a, vol)
+        assert S[0] == 1.0 and S[-1] == 0.0
+    assert 1.0 < studies.bl_welge(1.01)[1] < 1.01
+    assert 1.07 < studies.bl_welge(1.3)[1] < 1.08
+
+
+def _bl_oracle(ns, H=100, steps=100000, samples=20):
+    """The waterflooding set-up (displacement along x, F = 1e-4 along x,
+    coexistence densities held at both ends, uniform n_s, G_ads = 0; one
+    row, the y extent being periodic and the state uniform in y) on the
+    oracle.  Returns fronts (S = 0.5, as x), injected volume Q (trapezoid of
+    the medium's mean Eq. 7 velocity) and the last saturation profile."""
+    hi, lo = 0.98739, 0.03548
+    res = {0: (4, hi, lo), 1: (4, lo, hi)}
+    s = oracle.Sim(oracle.Params(H, 1, 1, tau=(1.0, 1.0), G=1.75, Fext=(1e-4, 0, 0),
+                                 reservoirs=res), np.full((1, 1, H), ns))
+    x = np.arange(H)
+    ra = np.where(x < 4, hi, lo)[None, None] * 1.0
+    s.init_equilibrium(ra, hi + lo - ra)
+    fronts, Q, q_prev = [4.0], [0.0], 0.0
+    for _ in range(samples):
+        s.step(steps // samples)
+        fl = s.fields()
+        S = (fl["rho_a"][0, 0] - lo) / (hi - lo)
+        q = float(fl["u"][0, 0, 0][4:H - 4].mean())
+        Q.append(Q[-1] + 0.5 * (q + q_prev) * (steps // samples))
+        q_prev = q
+        front = 4.0
+        for k in range(4, H - 1):
+            if S[k] >= 0.5 > S[k + 1]:
+                front = k + (S[k] - 0.5) / (S[k] - S[k + 1])
+                break
+        fronts.append(front)
+    return np.array(fronts), np.array(Q), S
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("ns, min_dQ", [(0.1, 20.0), (0.5, 2.5)])
+def test_buckley_leverett_front_between_the_papers_bounds(ns, min_dQ):
+    """The oracle's waterflooding over 100,000 steps: fluid 1 advances with
+    the Darcy flux (the injected volume grows by more than min_dQ lu), the
+    front's displacement over the last four fifths of the run lies between
+    the injected volume times the shock speed factors of the paper's bounds
+    a = 1.01 and 1.3, give or take 0.5 lu (the diffuse interface, ~3 lu
+    wide, settles by a fraction of a node), and behind the front the
+    saturation lies between the a = 1.3 profile and the (piston-like)
+    a = 1.01 one, ahead of it fluid 2 remains.  A dropped force term stops
+    the front; a wrong half-force term in Eq. 7 shifts q by ~12 % (more at
+    n_s = 0.5), which moves the band by more than 0.5 lu."""
+    from paper_2206_11524_gb300 import studies
+    fr, Q, S = _bl_oracle(ns)
+    k0 = 4
+    dQ = Q[-1] - Q[k0]
+    assert dQ > min_dQ, dQ
+    shift = fr[-1] - fr[k0]
+    lo_b, hi_b = studies.bl_welge(1.01)[1], studies.bl_welge(1.3)[1]
+    assert lo_b * dQ - 0.5 < shift < hi_b * dQ + 0.5, (shift, dQ)
+    x = np.arange(len(S))
+    behind = (x >= 4) & (x < fr[-1] - 3)
+    ahead = (x > fr[-1] + 3) & (x < len(S) - 4)
+    low = studies.bl_profile(x - 4.0, Q[-1], 1.3)
+    assert behind.sum() >= 2 and ahead.sum() >= 10
+    assert np.all(S[behind] >= low[behind] - 0.02), (S[behind], low[behind])
+    assert np.all(S[behind] <= 1.005)
+    assert np.all(np.abs(S[ahead]) <= 0.02)

@@ -11,9 +11,10 @@ library offers and for ragged and degenerate lattices:
   - a collision waits only on items of earlier groups when lag >= 3, and a
     greedy run of blocks that take tickets in order finishes (no deadlock),
     while lag = 2 can wait on a later item;
-  - several lattices in one launch (items numbered lattice by lattice) keep
-    every wait inside the waiting item's own lattice and on a smaller
-    ticket, and a greedy run of blocks finishes."""
+  - several lattices in one launch (items numbered group-major across the
+    batch, the segment arithmetic the launch uses checked against a plain
+    enumeration) keep every wait inside the waiting item's own lattice and on
+    a smaller ticket, and a greedy run of blocks finishes."""
 import pytest
 
 BY_OF_SHAPE = {1: 4, 2: 2, 3: 8}
@@ -139,24 +140,110 @@ def test_lag_two_can_wait_on_a_later_item():
     assert any(setter[fi] >= it["grp"] for it in items for fi in it["waits"])
 
 
-def _batch_schedule(sizes, by, lag):
-    """Items of several lattices numbered lattice by lattice (the batched
-    launch): each item's lattice, and its waits as (lattice, flag)."""
-    items, first = [], 0
-    for r, (nx, ny, nz) in enumerate(sizes):
-        its, tp, _, _ = schedule(nx, ny, nz, by, lag)
-        for it in its:
-            items.append({"r": r, "grp": it["grp"],
-                          "waits": [(r, f) for f in it["waits"]],
-                          "flag": (r, it["flag"]) if it["flag"] is not None else None})
-        first += len(its)
+def _batch_order(sizes, by, lag, budget=float("inf"), node_bytes=152):
+    """Lattices by group count, most first (stable), cut into sets whose
+    planes in flight ((lag + 2) planes of x-tile-padded rows) fit `budget`
+    bytes together (a lattice alone may exceed it); tiles per plane and
+    group counts."""
+    tps = [((nx + 31) // 32) * ((ny + by - 1) // by) for nx, ny, nz in sizes]
+    groups = [nz + lag for nx, ny, nz in sizes]
+    order = sorted(range(len(sizes)), key=lambda r: -groups[r])
+    sets, cur, used = [], [], 0.0
+    for r in order:
+        nx, ny, nz = sizes[r]
+        b = (lag + 2) * ((nx + 31) // 32) * 32 * ny * node_bytes
+        if cur and used + b > budget:
+            sets.append(cur)
+            cur, used = [], 0.0
+        cur.append(r)
+        used += b
+    sets.append(cur)
+    return sets, tps, groups
+
+
+def _segment_lookup(sizes, by, lag, budget=float("inf")):
+    """ticket -> (lattice, item of that lattice) by the launch's segment
+    arithmetic: inside each set, groups [G_m, G_(m-1)) hold the set's m
+    lattices with most groups, their tiles per plane summed per group."""
+    sets, tps, groups = _batch_order(sizes, by, lag, budget)
+    order = [r for st in sets for r in st]
+    tsum = [0]
+    for r in order:
+        tsum.append(tsum[-1] + tps[r])
+    segs, first, lb = [], 0, 0
+    for st in sets:
+        g0 = 0
+        for m in range(len(st), 0, -1):
+            gend = groups[order[lb + m - 1]]
+            if gend <= g0:
+                continue
+            segs.append((first, g0, lb, m))
+            first += (gend - g0) * (tsum[lb + m] - tsum[lb])
+            g0 = gend
+        lb += len(st)
+
+    def lookup(k):
+        s = max(i for i, sg in enumerate(segs) if sg[0] <= k)
+        f0, gs, lb, m = segs[s]
+        gg, rem = divmod(k - f0, tsum[lb + m] - tsum[lb])
+        rem += tsum[lb]
+        l = max(i for i in range(lb, lb + m) if tsum[i] <= rem)
+        r = order[l]
+        return r, (gs + gg) * tps[r] + rem - tsum[l]
+    return lookup, first
+
+
+def _batch_schedule(sizes, by, lag, budget=float("inf")):
+    """Items of several lattices in one launch: set after set, group-major
+    inside a set (group g of every lattice of the set that has one, in
+    order of group count, before group g + 1).  Each item's lattice, and
+    its waits as (lattice, flag)."""
+    sets, tps, groups = _batch_order(sizes, by, lag, budget)
+    per = [schedule(nx, ny, nz, by, lag)[0] for nx, ny, nz in sizes]
+    items = []
+    for st in sets:
+        for g in range(max(groups[r] for r in st)):
+            for r in st:
+                if g >= groups[r]:
+                    continue
+                for T in range(tps[r]):
+                    it = per[r][g * tps[r] + T]
+                    items.append({"r": r, "local": g * tps[r] + T, "grp": g,
+                                  "waits": [(r, f) for f in it["waits"]],
+                                  "flag": (r, it["flag"]) if it["flag"] is not None else None})
     return items
 
 
+BUDGETS = [float("inf"), 0.0, 2.0e6]
+
+
 @pytest.mark.parametrize("by", [2, 4])
-def test_batched_items_wait_inside_their_lattice(by):
+@pytest.mark.parametrize("budget", BUDGETS)
+def test_segment_arithmetic_numbers_the_batch(by, budget):
+    for sizes in ([(40, 9, 5), (7, 4, 3), (64, 20, 6), (33, 1, 2)],
+                  [(32, 32, 32), (64, 64, 64), (33, 7, 64), (96, 5, 1)],
+                  [(16, 3, 9)], [(8, 8, 4), (8, 8, 4), (40, 2, 4)]):
+        items = _batch_schedule(sizes, by, 4, budget)
+        lookup, total = _segment_lookup(sizes, by, 4, budget)
+        assert total == len(items) == sum((nz + 4) * ((nx + 31) // 32) * ((ny + by - 1) // by)
+                                           for nx, ny, nz in sizes)
+        assert [lookup(k) for k in range(total)] == [(it["r"], it["local"]) for it in items]
+        assert len({(it["r"], it["local"]) for it in items}) == total
+
+
+def test_sets_follow_the_budget():
+    sizes = [(32, 32, 32), (64, 64, 64), (33, 7, 64), (96, 5, 1)]
+    assert len(_batch_order(sizes, 2, 4)[0]) == 1
+    assert _batch_order(sizes, 2, 4, 0.0)[0] == [[1], [2], [0], [3]]
+    # 64^2 x 6 planes x 152 B = 3.7 MB: alone in a 2 MB set, the rest share
+    assert _batch_order(sizes, 2, 4, 2.0e6)[0] == [[1], [2, 0, 3]]
+
+
+@pytest.mark.parametrize("by", [2, 4])
+@pytest.mark.parametrize("budget", BUDGETS)
+def test_batched_items_wait_inside_their_lattice(by, budget):
     sizes = [(40, 9, 5), (7, 4, 3), (64, 20, 6), (33, 1, 2)]
-    items = _batch_schedule(sizes, by, 4)
+    items = _batch_schedule(sizes, by, 4, budget)
     setter = {it["flag"]: k for k, it in enumerate(items) if it["flag"] is not None}
     for k, it in enumerate(items):
         for wflag in it["waits"]:
