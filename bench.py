@@ -106,6 +106,54 @@ def _profiled_traffic(kernel):
     return bpn
 
 
+_UNIT_SCALE = {"byte": 1.0, "kbyte": 1e3, "mbyte": 1e6, "gbyte": 1e9, "tbyte": 1e12,
+               "nsecond": 1e-9, "usecond": 1e-6, "msecond": 1e-3, "second": 1.0,
+               "ns": 1e-9, "us": 1e-6, "ms": 1e-3, "s": 1.0}
+
+
+def record_traffic(csv_path, kernel, nodes):
+    """Per-launch DRAM bytes of `kernel` from an ncu --csv log of
+    dram__bytes_read.sum, dram__bytes_write.sum and gpu__time_duration.sum;
+    writes the machine-readable lines (source hash, bytes per node) of
+    profiles/<kernel>_electrode256.md and returns the per-launch rows."""
+    import csv
+    import re
+    rows = {}
+    with open(csv_path, newline="") as fh:
+        lines = [l for l in fh if l.startswith('"')]
+    for r in csv.DictReader(lines):
+        name = r.get("Kernel Name", "")
+        if name != kernel and not re.search(r"(^|[^A-Za-z0-9_])" + kernel + r"[<(]", name):
+            continue
+        key = r["ID"]
+        val = float(r["Metric Value"].replace(",", ""))
+        val *= _UNIT_SCALE.get(r["Metric Unit"].strip().lower(), 1.0)
+        rows.setdefault(key, {"kernel": name})[r["Metric Name"]] = val
+    out = []
+    for key in sorted(rows, key=int):
+        m = rows[key]
+        rd, wr = m["dram__bytes_read.sum"], m["dram__bytes_write.sum"]
+        out.append({"id": int(key), "kernel": m["kernel"],
+                    "us": m.get("gpu__time_duration.sum", float("nan")) * 1e6,
+                    "read_per_node": rd / nodes, "write_per_node": wr / nodes,
+                    "total_per_node": (rd + wr) / nodes})
+    if not out:
+        raise SystemExit(f"no launches of {kernel} in {csv_path}")
+    bpn = sum(r["total_per_node"] for r in out) / len(out)
+    short = kernel[2:] if kernel.startswith("k_") else kernel
+    path = os.path.join(ROOT, "profiles", f"{short}_electrode256.md")
+    text = open(path).read() if os.path.exists(path) else ""
+    keep = [l for l in text.splitlines()
+            if not l.startswith(("kernel_source_sha256_16:", "dram_bytes_per_node:"))]
+    while keep and not keep[-1].strip():
+        keep.pop()
+    keep += ["", f"kernel_source_sha256_16: {_kernel_sha()}",
+             f"dram_bytes_per_node: {bpn:.2f}"]
+    with open(path, "w") as fh:
+        fh.write("\n".join(keep) + "\n")
+    return out, bpn
+
+
 class ClockSampler:
     """nvidia-smi clock / throttle-reason sampling during the timed region."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -670,9 +718,23 @@ def main(argv=None):
     ap.add_argument("--large-s1-steps", type=int, default=400)
     ap.add_argument("--large-s1-every", type=int, default=50)
     ap.add_argument("--cpu-probe", type=float, default=0.0, help=argparse.SUPPRESS)
+    ap.add_argument("--record-traffic", default="",
+                    help="ncu --csv log of the DRAM-byte metrics: write the traffic lines "
+                         "of the kernel's profile summary (no GPU needed)")
+    ap.add_argument("--record-kernel", default="k_wave")
     args = ap.parse_args(argv)
     if args.cpu_probe > 0:
         return _cpu_probe(args.cpu_probe)
+    if args.record_traffic:
+        if args.shape:
+            nx, ny, nz = (int(v) for v in args.shape.split(","))
+        else:
+            nx = ny = nz = args.size
+        rows, bpn = record_traffic(args.record_traffic, args.record_kernel, nx * ny * nz)
+        for r in rows:
+            print(json.dumps(r))
+        print(json.dumps({"dram_bytes_per_node": bpn, "kernel_source_sha256_16": _kernel_sha()}))
+        return 0
     world, rank, local = _dist()
     if args.impl == "reference":
         return run_reference(args, world, rank)
