@@ -1000,7 +1000,15 @@ lbm_status batch_enqueue(lbm_ctx *const *ctxs, int n, int n_steps, cudaStream_t 
       a.prefix[k + 1] = a.prefix[k] + it.gx * it.gy * c->params.nz;
     }
     cudaError_t e = hmcsc::launch_batch_density(a, ctxs[0]->sp.storage, s);
-    if (e == cudaSuccess) e = hmcsc::launch_batch_collide(a, ctxs[0]->sp.storage, s);
+    // the fused pass in the first context's shapes: prefetching shapes run
+    // as one batched prefetching launch per AA parity present
+    const int ecfg = ctxs[0]->launch_cfg[1], ocfg = ctxs[0]->launch_cfg[2];
+    if (e == cudaSuccess) {
+      if (ecfg >= hmcsc::kCollidePipeFirst && ocfg >= hmcsc::kCollidePipeFirst)
+        e = hmcsc::launch_batch_collide_pipe(a, ctxs[0]->sp.storage, ecfg, ocfg, s);
+      else
+        e = hmcsc::launch_batch_collide(a, ctxs[0]->sp.storage, s);
+    }
     if (e != cudaSuccess) {
       for (int k = 0; k < n; ++k) cuda_fail(ctxs[k], e, "batched kernel");
       return LBM_ECUDA;

@@ -606,10 +606,12 @@ __device__ __forceinline__ void cp_async_wait() {
 }
 
 
+// The fused pass of one block of a prefetching shape: x-tile bx, rows
+// [by0 * by, by0 * by + by) and the run of planes [bz * zc, bz * zc + zc)
+// of lattice (p, w).
 template <int PARITY, int ST, bool PC, int CFG>
-__global__ void __launch_bounds__(CollideShape<PARITY, ST, CFG>::threads,
-                                  CollideShape<PARITY, ST, CFG>::s.minb)
-    k_collide_pipe(StepParams p, Workspace w) {
+__device__ __forceinline__ void pipe_block(const StepParams &p, const Workspace &w, int bx,
+                                           int by0, int bz) {
   using C = Codec2<ST>;
   using T2 = typename C::T2;
   constexpr Shape S = CollideShape<PARITY, ST, CFG>::s;
@@ -623,9 +625,9 @@ __global__ void __launch_bounds__(CollideShape<PARITY, ST, CFG>::threads,
   float *ring_a = reinterpret_cast<float *>(ring_rho + kPipeRingPlanes * R * RC);
   float *ring_b = ring_a + kPipeRingPlanes * R * RC;
   const int tid = threadIdx.y * kTile + threadIdx.x;
-  const int x = blockIdx.x * kTile + threadIdx.x, y = blockIdx.y * S.by + threadIdx.y;
-  const int z0 = blockIdx.z * ZC, zend = min(z0 + ZC, p.nz);
-  const int xlo = blockIdx.x * kTile, ylo = blockIdx.y * S.by;
+  const int x = bx * kTile + threadIdx.x, y = by0 * S.by + threadIdx.y;
+  const int z0 = bz * ZC, zend = min(z0 + ZC, p.nz);
+  const int xlo = bx * kTile, ylo = by0 * S.by;
   const bool maybe_res = box_in_reservoir(p, xlo, min(xlo + kTile, p.nx) - 1, ylo,
                                           min(ylo + S.by, p.ny) - 1, z0, zend - 1);
   const bool active = x < p.nx && y < p.ny;
@@ -728,6 +730,13 @@ __global__ void __launch_bounds__(CollideShape<PARITY, ST, CFG>::threads,
       collide_loaded<PARITY, ST, PC, SmemStencil, S.cs>(p, w, g, st, f1, f2);
     }
   }
+}
+
+template <int PARITY, int ST, bool PC, int CFG>
+__global__ void __launch_bounds__(CollideShape<PARITY, ST, CFG>::threads,
+                                  CollideShape<PARITY, ST, CFG>::s.minb)
+    k_collide_pipe(StepParams p, Workspace w) {
+  pipe_block<PARITY, ST, PC, CFG>(p, w, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 template <int PARITY, int ST, int CFG, bool PC>
@@ -1274,6 +1283,21 @@ __global__ void __launch_bounds__(kTile * kBatchBY, CollideShape<1, ST, 0>::s.mi
     collide_body<0, ST, PC>(it.p, it.w, maybe_res, x, y, z);
   else
     collide_body<1, ST, PC>(it.p, it.w, maybe_res, x, y, z);
+}
+
+// The prefetching fused pass over a batch of lattices at one AA parity:
+// item r's blocks (prefix[r] .. prefix[r + 1]) tile its lattice as
+// k_collide_pipe's grid does for shape CFG (gx x-tiles, gy row groups, runs
+// of zc planes), and each block runs that kernel's body on its lattice.
+template <int PARITY, int ST, bool PC, int CFG>
+__global__ void __launch_bounds__(CollideShape<PARITY, ST, CFG>::threads,
+                                  CollideShape<PARITY, ST, CFG>::s.minb)
+    k_batch_collide_pipe(const __grid_constant__ BatchArgs a) {
+  const int r = batch_item_of_block(a);
+  const BatchItem &it = a.item[r];
+  const int lb = blockIdx.x - a.prefix[r];
+  const int rest = lb / it.gx;
+  pipe_block<PARITY, ST, PC, CFG>(it.p, it.w, lb % it.gx, rest % it.gy, rest / it.gy);
 }
 
 }  // namespace

@@ -283,6 +283,12 @@ struct BatchArgs {
 static_assert(sizeof(BatchArgs) <= 32000, "kernel parameter limit");
 cudaError_t launch_batch_density(const BatchArgs &a, int storage, cudaStream_t s);
 cudaError_t launch_batch_collide(const BatchArgs &a, int storage, cudaStream_t s);
+// The prefetching fused pass over a batch (k_batch_collide_pipe): one launch
+// per AA parity present among the items, shapes even_cfg / odd_cfg (both >=
+// kCollidePipeFirst); the items' gx, gy and the prefix table of `a` are
+// not used (each launch lays out its own blocks).
+cudaError_t launch_batch_collide_pipe(const BatchArgs &a, int storage, int even_cfg,
+                                      int odd_cfg, cudaStream_t s);
 
 // One batched wavefront step (k_wave_batch, one launch per AA parity
 // present) over n lattices of one storage kind: lattice k's parameters,
@@ -321,7 +327,8 @@ constexpr double kWaveSetL2Share = 0.5;
                                 int, int, unsigned, long long, cudaStream_t);  \
   cudaError_t launch_wave_batch_##SUF(const WaveJob &, cudaStream_t);         \
   cudaError_t launch_batch_density_##SUF(const BatchArgs &, cudaStream_t);     \
-  cudaError_t launch_batch_collide_##SUF(const BatchArgs &, cudaStream_t);
+  cudaError_t launch_batch_collide_##SUF(const BatchArgs &, cudaStream_t);     \
+  cudaError_t launch_batch_collide_pipe_##SUF(const BatchArgs &, int, int, cudaStream_t);
 HMCSC_DECLARE_STORAGE_LAUNCHERS(f32)
 HMCSC_DECLARE_STORAGE_LAUNCHERS(f16)
 HMCSC_DECLARE_STORAGE_LAUNCHERS(bf16)

@@ -235,6 +235,19 @@ cudaError_t launch_wave_batch(const WaveJob &job, int storage, cudaStream_t s) {
   }
 }
 
+cudaError_t launch_batch_collide_pipe(const BatchArgs &a, int storage, int even_cfg,
+                                      int odd_cfg, cudaStream_t s) {
+  if (a.n <= 0) return cudaSuccess;
+  if (even_cfg < kCollidePipeFirst || odd_cfg < kCollidePipeFirst) return cudaErrorInvalidValue;
+  switch (storage) {
+    case kF16: return launch_batch_collide_pipe_f16(a, even_cfg, odd_cfg, s);
+    case kBF16: return launch_batch_collide_pipe_bf16(a, even_cfg, odd_cfg, s);
+    case kF16L: return launch_batch_collide_pipe_f16l(a, even_cfg, odd_cfg, s);
+    case kBF16L: return launch_batch_collide_pipe_bf16l(a, even_cfg, odd_cfg, s);
+    default: return launch_batch_collide_pipe_f32(a, even_cfg, odd_cfg, s);
+  }
+}
+
 cudaError_t launch_batch_density(const BatchArgs &a, int storage, cudaStream_t s) {
   if (a.n <= 0 || a.prefix[a.n] <= 0) return cudaSuccess;
   switch (storage) {

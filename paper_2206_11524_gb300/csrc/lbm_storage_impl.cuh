@@ -362,6 +362,63 @@ cudaError_t HMCSC_NAME(launch_batch_density)(const BatchArgs &a, cudaStream_t s)
   return cudaGetLastError();
 }
 
+namespace {
+// k_batch_collide_pipe over the items of `a` at AA parity PARITY, shape CFG.
+template <int PARITY, bool PC, int CFG>
+cudaError_t batch_pipe_launch(const BatchArgs &a, cudaStream_t s) {
+  using T2 = typename Codec2<kST>::T2;
+  constexpr Shape S = CollideShape<PARITY, kST, CFG>::s;
+  constexpr PipeCfg P = pipe_cfg(CFG);
+  constexpr int smem = pipe_smem_bytes(CFG, (int)sizeof(T2), PC);
+  static thread_local BatchArgs b;  // ~16 KB: kept off the stack
+  b.n = 0;
+  b.prefix[0] = 0;
+  for (int k = 0; k < a.n; ++k) {
+    if ((a.item[k].parity & 1) != PARITY) continue;
+    BatchItem &it = b.item[b.n];
+    it = a.item[k];
+    it.gx = it.p.ntx;
+    it.gy = (it.p.ny + S.by - 1) / S.by;
+    const long long blocks =
+        (long long)b.prefix[b.n] + (long long)it.gx * it.gy * ((it.p.nz + P.zc - 1) / P.zc);
+    if (blocks > 2147483647LL) return cudaErrorInvalidValue;
+    b.prefix[b.n + 1] = (int)blocks;
+    ++b.n;
+  }
+  if (b.n == 0) return cudaSuccess;
+  static std::once_flag attr_once;
+  static cudaError_t attr_err = cudaSuccess;
+  std::call_once(attr_once, [] {
+    attr_err = cudaFuncSetAttribute(k_batch_collide_pipe<PARITY, kST, PC, CFG>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  });
+  if (attr_err != cudaSuccess) return attr_err;
+  k_batch_collide_pipe<PARITY, kST, PC, CFG>
+      <<<(unsigned)b.prefix[b.n], dim3(kTile, S.by, 1), smem, s>>>(b);
+  return cudaGetLastError();
+}
+template <int PARITY, bool PC>
+cudaError_t batch_pipe_any(const BatchArgs &a, int cfg, cudaStream_t s) {
+  switch (cfg) {
+    case 5: return batch_pipe_launch<PARITY, PC, 5>(a, s);
+    case 6: return batch_pipe_launch<PARITY, PC, 6>(a, s);
+    case 7: return batch_pipe_launch<PARITY, PC, 7>(a, s);
+    case 8: return batch_pipe_launch<PARITY, PC, 8>(a, s);
+    case 9: return batch_pipe_launch<PARITY, PC, 9>(a, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+}  // namespace
+
+cudaError_t HMCSC_NAME(launch_batch_collide_pipe)(const BatchArgs &a, int even_cfg, int odd_cfg,
+                                                  cudaStream_t s) {
+  const bool pc = a.item[0].w.ns2 != nullptr;
+  cudaError_t e = pc ? batch_pipe_any<0, true>(a, even_cfg, s)
+                     : batch_pipe_any<0, false>(a, even_cfg, s);
+  if (e != cudaSuccess) return e;
+  return pc ? batch_pipe_any<1, true>(a, odd_cfg, s) : batch_pipe_any<1, false>(a, odd_cfg, s);
+}
+
 cudaError_t HMCSC_NAME(launch_batch_collide)(const BatchArgs &a, cudaStream_t s) {
   const dim3 grid((unsigned)a.prefix[a.n]), block(kTile, kBatchBY, 1);
   if (a.item[0].w.ns2)

@@ -844,3 +844,63 @@ def test_buckley_leverett_front_between_the_papers_bounds(ns, min_dQ):
     assert np.all(S[behind] >= low[behind] - 0.02), (S[behind], low[behind])
     assert np.all(S[behind] <= 1.005)
     assert np.all(np.abs(S[ahead]) <= 0.02)
+
+
+# --------------------------------------------------------------------------
+# Sessile droplet contact angle against Eq. 15 (Sec. 3.4, Table 3's theta_H)
+# --------------------------------------------------------------------------
+
+def _sessile_theta(gads, nx=80, ny=48, R=14, steps=12000, wall=3):
+    """A 2D droplet of fluid 1 (coexistence densities at G = 1.75) started
+    as a half disc on a wall of `wall` rows with n_s = 1 and adhesion
+    G_ads,2 = gads (a second, neutral wall closes the top; x periodic); the
+    wall cells start nearly empty (1e-6 of each fluid: solid nodes without
+    fluid, as in the multicomponent Shan-Chen droplets Eq. 15 was derived
+    from; an empty cell has no velocity, Eq. 6).  The angle of the circular
+    cap from its height h on the centre column and the half-width a of its
+    base on the first fluid row: theta = 2 atan(h / a)."""
+    hi, lo = 0.98739, 0.03548
+    ns = np.zeros((1, ny, nx))
+    ga = np.zeros((1, ny, nx))
+    ns[0, :wall] = 1.0
+    ga[0, :wall] = gads
+    ns[0, ny - wall:] = 1.0
+    y, x = np.mgrid[0:ny, 0:nx]
+    r = np.hypot(x - (nx / 2 - 0.5), y - (wall - 0.5))
+    ra = np.where((r < R) & (y >= wall), hi, lo)[None] * 1.0
+    rb = hi + lo - ra
+    ra[ns > 0.5] = 1e-6
+    rb[ns > 0.5] = 1e-6
+    s = oracle.Sim(oracle.Params(nx, ny, 1, tau=(1.0, 1.0), G=1.75), ns, ga)
+    s.init_equilibrium(ra, rb)
+    s.step(steps)
+    r1 = s.fields()["rho_a"][0]
+    mid = 0.5 * (hi + lo)
+    col = 0.5 * (r1[:, nx // 2 - 1] + r1[:, nx // 2])
+    h = next(k + (col[k] - mid) / (col[k] - col[k + 1]) for k in range(wall, ny - 1)
+             if col[k] >= mid > col[k + 1]) - (wall - 0.5)
+    row = r1[wall]
+    xs = [k + (row[k] - mid) / (row[k] - row[k + 1]) for k in range(nx - 1)
+          if (row[k] - mid) * (row[k + 1] - mid) < 0]
+    a = (max(xs) - min(xs)) / 2
+    return math.degrees(2 * math.atan2(h, a))
+
+
+@pytest.mark.slow
+def test_sessile_droplet_contact_angle_follows_eq15():
+    """The oracle's sessile droplets against Eq. 15, cos theta_H = 4 G_ads,2
+    / (G (rho_1 - rho_dis,2)): a neutral wall gives 90 deg (within 3), and
+    G_ads,2 = +-0.2 give angles within 10 deg of theta_H = 61.3 / 118.7 deg
+    (the paper calls the correlation approximate and sees deviations of
+    this size, Table 3), on the right side of 90.  A sign error in the
+    adhesion force swaps the two; a dropped adhesion term leaves all at
+    90; adhesion half as strong gives 72.8 deg at G_ads,2 = 0.2 (11.5 off),
+    twice as strong spreads the droplet into a film."""
+    hi, lo, G = 0.98739, 0.03548, 1.75
+    th0 = _sessile_theta(0.0)
+    assert abs(th0 - 90.0) < 3.0, th0
+    for gads in (0.2, -0.2):
+        th = _sessile_theta(gads)
+        th_h = math.degrees(math.acos(4 * gads / (G * (hi - lo))))
+        assert abs(th - th_h) < 10.0, (gads, th, th_h)
+        assert (th < th0) == (gads > 0), (gads, th, th0)
