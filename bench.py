@@ -349,8 +349,9 @@ def _lattice_for(case, storage, stream):
     return lat
 
 
-# launch shapes (density, even, odd) measured fastest per storage; the
-# 16-bit storages keep the two-pass step (their wavefront step is slower)
+# Two-pass launch shapes (density, even, odd) measured fastest per storage
+# on the benchmark lattice (the 16-bit storages keep the two-pass step:
+# their wavefront step is slower)
 DEFAULT_LAUNCH = {"f32": (1, 6, 7), "f16": (0, 6, 8), "bf16": (0, 6, 8),
                   "f16l": (0, 9, 9), "bf16l": (0, 9, 9)}
 
@@ -375,8 +376,10 @@ def _time_two_pass(lat, steps, stream):
 
 
 def storage_record(case, storage, steps, warmup, peak):
-    """Two-pass step of one 16-bit storage on the benchmark lattice: MLUPS and
-    the fused pass's roofline on its own algorithmic bytes."""
+    """Two-pass step of one population storage on the benchmark lattice
+    (float32 included: its fused pass is the fused step of the method, timed
+    apart from the wavefront launch the headline uses): MLUPS and the fused
+    pass's roofline on its own algorithmic bytes."""
     import torch
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
@@ -708,8 +711,9 @@ def main(argv=None):
     ap.add_argument("--serve-steps-min", type=int, default=312)
     ap.add_argument("--serve-steps-max", type=int, default=2500)
     ap.add_argument("--serve-storage", default="f16")
-    ap.add_argument("--storages", default="f16,f16l",
-                    help="16-bit storages timed on the same lattice (comma list; '' skips)")
+    ap.add_argument("--storages", default="f32,f16,f16l",
+                    help="storages whose two-pass step is timed on the same lattice "
+                         "(comma list; '' skips)")
     ap.add_argument("--storage-steps", type=int, default=40)
     ap.add_argument("--large-shape", default="512,512,384",
                     help="nx,ny,nz of the large single-domain record ('' skips)")

@@ -830,14 +830,14 @@ __global__ void k_init_equilibrium(StepParams p, Workspace w,
 // The lattice is cut into items: tile T (32 x by nodes of one plane) of
 // group g, g = 0 .. nz + lag - 1, numbered group-major and taken by the
 // blocks in the order of an atomic ticket.  Item (g, T)
-//   - copies the populations of plane d(g) = (g - 1) mod nz of T (if
-//     g < nz) and of plane q = g - lag of T (if q >= 0) into shared memory,
-//   - sums the populations of plane d(g) into the density array and
-//     publishes them: after a block barrier one thread sets the flag of
-//     (d(g), T) to the launch's epoch with a release store,
+//   - copies the populations of plane q = g - lag of T (if q >= 0) and of
+//     plane d(g) = (g - 1) mod nz of T (if g < nz) into shared memory,
 //   - waits until the densities of planes q - 1 .. q + 1 of T and of its
 //     eight in-plane neighbour tiles are published, then collides and
-//     streams plane q of T exactly as k_collide_stream does.
+//     streams plane q of T exactly as k_collide_stream does,
+//   - sums the populations of plane d(g) into the density array and
+//     publishes them: after a block barrier one thread sets the flag of
+//     (d(g), T) to the launch's epoch with a release store.
 // The densities a collision of plane q needs come from groups q .. q + 2,
 // all before g when lag >= 3, so an item waits only on items with smaller
 // tickets; those are held by blocks that are already running, so the launch
@@ -917,9 +917,8 @@ struct WaveRho : GlobalRho {
 // One wavefront item: ticket k of the launch's lattice (p, w).  buf is the
 // block's two population buffers (this thread's own slots: [b][i][tid]),
 // epoch the lattice's launch epoch, hold a flag left unpublished (-1: none;
-// failure-path tests).  The item sums and publishes its plane (one block
-// barrier, which also orders the reads of the block's ticket) before it
-// waits and collides; it returns with this thread's buffer slots free.
+// failure-path tests).  Ends after a block barrier with the tile's densities
+// stored and published and the buffers free.
 template <int PARITY, int ST, bool PC, int BY>
 __device__ __forceinline__ void wave_tile_item(const StepParams &p, const Workspace &w,
                                                unsigned k, const WaveArgs &a, long long hold,
@@ -966,31 +965,11 @@ __device__ __forceinline__ void wave_tile_item(const StepParams &p, const Worksp
   const bool has_c = q >= 0, has_d = grp < p.nz;
   const int xlo = tx * kTile, xhi = min(xlo + kTile, p.nx) - 1;
   const int ylo = ty * BY, yhi = min(ylo + BY, p.ny) - 1;
-  // one commit group per plane: the density part's first
-  if (has_d && active) copy(x, y, zd, 1);
-  cp_async_commit();
+  // one commit group per plane: the collision's first
   if (has_c && active) copy(x, y, q, 0);
   cp_async_commit();
-  // Sum and publish plane zd before waiting for the collision's densities:
-  // publication never waits on anything, and the release below then waits
-  // only for the density stores, not for the collision's population stores.
-  // The two halves touch disjoint populations (planes zd and q, each node's
-  // own pairs).
-  cp_async_wait<1>();  // this thread's copies of plane zd have landed
-  if (has_d && active) {
-    const long long own = ((long long)(zd * p.ny + y) * p.ntx + tx) * kTile + threadIdx.x;
-    float v1[kQ], v2[kQ];
-    decode(1, (int)own, v1, v2);
-    reservoir_state(p, box_in_reservoir(p, xlo, xhi, ylo, yhi, zd, zd), x, y, zd, v1, v2);
-    if (in_bounds(w.fault, own, nodes, kFaultRhoStore))
-      w.rho[own] = make_float2(sum19(v1), sum19(v2));
-  }
-  __syncthreads();  // the tile's densities are stored
-  if (has_d && tid == 0) {
-    long long fi = (long long)zd * a.tp + T;
-    if (fi != hold && (!kChecked || in_bounds(w.fault, fi, nflags, kFaultFlag)))
-      st_release(&flag[fi], epoch);
-  }
+  if (has_d && active) copy(x, y, zd, 1);
+  cp_async_commit();
   // every warp waits for the 27 tiles' densities itself
   if (has_c && threadIdx.x < 27) {
     const int l = threadIdx.x;
@@ -1011,16 +990,29 @@ __device__ __forceinline__ void wave_tile_item(const StepParams &p, const Worksp
     }
   }
   __syncwarp();  // the densities this warp's collisions read are published
-  cp_async_wait<0>();
   if (has_c && active) {
+    cp_async_wait<1>();
     const Geo g = make_geo(p, x, y, q);
     float f1[kQ], f2[kQ];
     decode(0, g.node(0, 0, 0), f1, f2);
     reservoir_state(p, box_in_reservoir(p, xlo, xhi, ylo, yhi, q, q), x, y, q, f1, f2);
     collide_loaded<PARITY, ST, PC, WaveRho>(p, w, g, WaveRho{global_rho(p, w, g)}, f1, f2);
   }
-  // Each thread reads and refills only its own buffer slots, so the next
-  // item needs no barrier here; its tickets are read after its own barrier.
+  cp_async_wait<0>();
+  if (has_d && active) {
+    const long long own = ((long long)(zd * p.ny + y) * p.ntx + tx) * kTile + threadIdx.x;
+    float v1[kQ], v2[kQ];
+    decode(1, (int)own, v1, v2);
+    reservoir_state(p, box_in_reservoir(p, xlo, xhi, ylo, yhi, zd, zd), x, y, zd, v1, v2);
+    if (in_bounds(w.fault, own, nodes, kFaultRhoStore))
+      w.rho[own] = make_float2(sum19(v1), sum19(v2));
+  }
+  __syncthreads();  // the tile's densities are stored, the buffers free
+  if (has_d && tid == 0) {
+    long long fi = (long long)zd * a.tp + T;
+    if (fi != hold && (!kChecked || in_bounds(w.fault, fi, nflags, kFaultFlag)))
+      st_release(&flag[fi], epoch);
+  }
 }
 
 // The last block out resets the ticket and done counter (in ctl) and
@@ -1066,7 +1058,6 @@ __global__ void __launch_bounds__(WaveShape<ST, CFG>::threads, WaveShape<ST, CFG
     wave_tile_item<PARITY, ST, PC, BY>(p, w, k, a, a.hold, buf, epoch);
     k = s_ticket[it];
   }
-  __syncthreads();  // every item of the block is done before it counts out
   unsigned *ctls[1] = {ctl};
   wave_exit(ctl, ctls, 1);
 }

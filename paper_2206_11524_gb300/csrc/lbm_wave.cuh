@@ -113,7 +113,6 @@ __global__ void __launch_bounds__(WaveShape<ST, CFG>::threads, WaveShape<ST, CFG
     wave_tile_item<PARITY, ST, PC, BY>(L.p, L.w, local, a, hold, buf, s_epoch[r]);
     k = s_ticket[it];
   }
-  __syncthreads();  // every item of the block is done before it counts out
   wave_exit(ctl0, s_ctls, b.n);
 }
 

@@ -327,6 +327,20 @@ def summarize(results):
             "mlups": work / (end - start) / 1e6}
 
 
+def result_differences(results, reference):
+    """Per request, the batched result against the reference arm's (same
+    request, same steps): absolute difference of S_1 (Eq. 19) and relative
+    difference of each component's mass; max and median over the trace."""
+    ref = {r.rid: r.obs for r in reference}
+    ds, dm = [], []
+    for r in results:
+        o = ref[r.rid]
+        ds.append(abs(r.obs["sat1"] - o["sat1"]))
+        dm.append(max(abs(a / b - 1.0) for a, b in zip(r.obs["mass"], o["mass"]) if b))
+    return {"sat1_abs_max": float(np.max(ds)), "sat1_abs_median": float(np.median(ds)),
+            "mass_rel_max": float(np.max(dm)), "mass_rel_median": float(np.median(dm))}
+
+
 def compare(n_req=24, L_min=32, L_max=160, steps_min=1000, steps_max=6000,
             storage="f16", load=0.9, seed=2206, tick_steps=400, overload=True,
             wave=WAVE_BATCH):
@@ -335,7 +349,8 @@ def compare(n_req=24, L_min=32, L_max=160, steps_min=1000, steps_max=6000,
     three median-size requests of the trace): the arrival times are Poisson
     at that rate.  With `overload`, both arms also run the trace with every
     request arriving at t = 0, which shows capacity (aggregate MLUPS) rather
-    than the arrival rate.  Returns the summaries and the trace description."""
+    than the arrival rate.  Returns the summaries, the trace description and
+    how far the batched results (in `storage`) lie from the float32 ones."""
     reqs = make_requests(n_req=n_req, seed=seed, L_min=L_min, L_max=L_max,
                          steps_min=steps_min, steps_max=steps_max, base_n=L_max)
     out = {}
@@ -361,9 +376,11 @@ def compare(n_req=24, L_min=32, L_max=160, steps_min=1000, steps_max=6000,
     for r in reqs:
         t += float(rng.exponential(1.0 / rate))
         r.arrival = t
-    seq = summarize(run_sequential(reqs, wave=wave))
+    seq_res = run_sequential(reqs, wave=wave)
+    seq = summarize(seq_res)
     srv = Server(storage=storage, tick_steps=tick_steps, wave=wave)
-    bat = summarize(srv.run(reqs))
+    bat_res = srv.run(reqs)
+    bat = summarize(bat_res)
     bat.update(storage=storage, graph_launches=srv.graph_launches,
                captures=srv.captures, ticks=srv.ticks)
     seq.update(storage="f32")
@@ -374,5 +391,6 @@ def compare(n_req=24, L_min=32, L_max=160, steps_min=1000, steps_max=6000,
                          "wettability",
                 "step": ("persistent wavefront launch over the batch" if wave
                          else "two batched passes (density, fused) per step"),
-                "batched": bat, "sequential": seq})
+                "batched": bat, "sequential": seq,
+                "batched_vs_sequential_f32": result_differences(bat_res, seq_res)})
     return out
