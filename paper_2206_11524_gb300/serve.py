@@ -2,21 +2,22 @@
 
 Requests (a lattice, its geometry and wettability, G, a step budget) arrive
 over time.  The server keeps every admitted simulation resident in HBM, runs
-a batch of them together -- by default one persistent wavefront launch per
-time step over every lattice of the batch (row tiles of all lattices taken
-from one ticket), else one batched density launch and one batched fused
-launch per step -- captured as CUDA graphs of an even number of steps,
-admits new requests between ticks as memory and batch slots free up, and
-returns each result (the observables of its final state) as soon as its step
-budget is spent.  Host-side uploads of newly admitted requests overlap with
-the batch running on the GPU.
+a batch of them together -- one batched density launch and one batched
+prefetching fused launch per time step and AA parity over every lattice of
+the batch (lbm_batch_step; for lattices on the wavefront step, one
+persistent launch per step over all of them instead) -- captured as CUDA
+graphs of an even number of steps, admits new requests between ticks as
+memory and batch slots free up, and returns each result (the observables of
+its final state) as soon as its step budget is spent.  Host-side uploads of
+newly admitted requests overlap with the batch running on the GPU.
 
 `run_sequential` is the one-at-a-time baseline on the same arrival trace:
 each request alone, float32 storage, first come first served, with the
-single-lattice step given (the batched wavefront launch by default).
+library's single-lattice step.
 
 Metrics: time-to-result (arrival -> result on the host) per request, its
-p50 / p99, and aggregate MLUPS = sum(nodes x steps) / makespan.
+p50 / p99, aggregate MLUPS = sum(nodes x steps) / makespan, and how far the
+batched results lie from the baseline's.
 """
 from __future__ import annotations
 
@@ -331,12 +332,12 @@ def result_differences(results, reference):
     """Per request, the batched result against the reference arm's (same
     request, same steps): absolute difference of S_1 (Eq. 19) and relative
     difference of each component's mass; max and median over the trace."""
-    ref = {r.rid: r.obs for r in reference}
+    ref = {r.rid: r.observables for r in reference}
     ds, dm = [], []
     for r in results:
         o = ref[r.rid]
-        ds.append(abs(r.obs["sat1"] - o["sat1"]))
-        dm.append(max(abs(a / b - 1.0) for a, b in zip(r.obs["mass"], o["mass"]) if b))
+        ds.append(abs(r.observables["sat1"] - o["sat1"]))
+        dm.append(max(abs(a / b - 1.0) for a, b in zip(r.observables["mass"], o["mass"]) if b))
     return {"sat1_abs_max": float(np.max(ds)), "sat1_abs_median": float(np.median(ds)),
             "mass_rel_max": float(np.max(dm)), "mass_rel_median": float(np.median(dm))}
 

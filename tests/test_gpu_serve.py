@@ -97,8 +97,11 @@ def _lattices(storage, shapes=((20, 12, 40), (8, 30, 64), (17, 9, 33)), wave=0):
 
 
 @pytest.mark.parametrize("wave", [0, 2])
-@pytest.mark.parametrize("storage", ["f32", "f16l"])
+@pytest.mark.parametrize("storage", ["f32", "f16", "f16l"])
 def test_batch_step_equals_single_steps(storage, wave):
+    """Batched steps equal single steps bit for bit, also while the
+    lattices of one batched call are at different AA parities (one launch
+    per parity present)."""
     alone = _lattices(storage)
     mixed = _lattices(storage, wave=wave)
     for g in alone:
@@ -106,9 +109,10 @@ def test_batch_step_equals_single_steps(storage, wave):
     stream = torch.cuda.Stream()
     torch.cuda.synchronize()
     lbm.lbm_batch_step([g.ctx for g in mixed], 3, stream.cuda_stream)
-    lbm.lbm_batch_step([g.ctx for g in mixed[1:]], 1, stream.cuda_stream)  # parities differ now
-    lbm.lbm_batch_step([mixed[0].ctx], 1, stream.cuda_stream)
+    lbm.lbm_batch_step([g.ctx for g in mixed[1:]], 1, stream.cuda_stream)
+    # parities differ now: lattice 0 at t = 3, the others at t = 4
     lbm.lbm_batch_step([g.ctx for g in mixed], 3, stream.cuda_stream)
+    lbm.lbm_batch_step([mixed[0].ctx], 1, stream.cuda_stream)
     stream.synchronize()
     for a, b in zip(alone, mixed):
         assert a.t == b.t == 7

@@ -124,3 +124,19 @@ def test_droplet_measurement_helpers():
     assert abs(R - R0) < 0.02 * R0
     p = np.where(case.rho_a > 0.5, 0.31, 0.30)
     assert abs(studies.pressure_jump(p, R) - 0.01) < 1e-12
+
+
+def test_serving_result_differences():
+    """The batched-versus-float32 comparison matches requests by id and
+    reports the largest and median S_1 and relative mass differences."""
+    from paper_2206_11524_gb300 import serve
+
+    def res(rid, sat1, mass):
+        return serve.Result(rid, 0.0, 0.0, 1.0, 8, 2, {"sat1": sat1, "mass": mass})
+    ref = [res(0, 0.5, (10.0, 2.0)), res(1, 0.25, (4.0, 4.0)), res(2, 0.0, (1.0, 1.0))]
+    got = [res(2, 0.001, (1.0, 1.0)), res(0, 0.5, (10.0, 2.01)), res(1, 0.2, (4.4, 4.0))]
+    d = serve.result_differences(got, ref)
+    assert abs(d["sat1_abs_max"] - 0.05) < 1e-12
+    assert abs(d["sat1_abs_median"] - 0.001) < 1e-12
+    assert abs(d["mass_rel_max"] - 0.1) < 1e-12
+    assert abs(d["mass_rel_median"] - 0.005) < 1e-12
