@@ -326,11 +326,13 @@ def serving_leg(args):
     (two passes each) on the same seeded trace of heterogeneous requests:
     the trace shape of the serving workload (cubic L log-uniform in [32,
     192]) with fewer requests and step budgets scaled down, offered at 0.9
-    of the sequential capacity and with every request arriving at once."""
+    of the sequential capacity and with every request arriving at once; the
+    capacity run also serves the local-offset storage (f16l)."""
     from paper_2206_11524_gb300 import serve
     out = serve.compare(n_req=args.serve_requests, L_min=32, L_max=args.serve_lmax,
                         steps_min=args.serve_steps_min, steps_max=args.serve_steps_max,
-                        storage=args.serve_storage, load=0.9, seed=2206, overload=True)
+                        storage=args.serve_storage, load=0.9, seed=2206, overload=True,
+                        overload_storages=("f16l",))
     out["config"] = (f"{args.serve_requests} requests, L in [32, {args.serve_lmax}], steps "
                      f"U{{{args.serve_steps_min}..{args.serve_steps_max}}} (the 5,000-40,000 "
                      f"of the full trace scaled by {args.serve_steps_max / 40000:.3g})")

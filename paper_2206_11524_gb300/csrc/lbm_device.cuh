@@ -1285,13 +1285,24 @@ __global__ void __launch_bounds__(kTile * kBatchBY, CollideShape<1, ST, 0>::s.mi
     collide_body<1, ST, PC>(it.p, it.w, maybe_res, x, y, z);
 }
 
+// Blocks per SM the batched prefetching pass is compiled for: those of the
+// single-lattice kernel, except the local storages' odd step in shape 9,
+// whose budget (6 blocks, up to 170 registers) lets the lattice lookup take
+// it to 137 registers and 7 resident blocks; held to 8 blocks (128
+// registers) it needs no spill.
+template <int PARITY, int ST, int CFG>
+__host__ __device__ constexpr int batch_pipe_minb() {
+  return (storage_local(ST) && PARITY == 1 && CFG == 9) ? 8
+                                                        : CollideShape<PARITY, ST, CFG>::s.minb;
+}
+
 // The prefetching fused pass over a batch of lattices at one AA parity:
 // item r's blocks (prefix[r] .. prefix[r + 1]) tile its lattice as
 // k_collide_pipe's grid does for shape CFG (gx x-tiles, gy row groups, runs
 // of zc planes), and each block runs that kernel's body on its lattice.
 template <int PARITY, int ST, bool PC, int CFG>
 __global__ void __launch_bounds__(CollideShape<PARITY, ST, CFG>::threads,
-                                  CollideShape<PARITY, ST, CFG>::s.minb)
+                                  batch_pipe_minb<PARITY, ST, CFG>())
     k_batch_collide_pipe(const __grid_constant__ BatchArgs a) {
   const int r = batch_item_of_block(a);
   const BatchItem &it = a.item[r];

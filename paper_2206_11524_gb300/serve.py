@@ -344,28 +344,33 @@ def result_differences(results, reference):
 
 def compare(n_req=24, L_min=32, L_max=160, steps_min=1000, steps_max=6000,
             storage="f16", load=0.9, seed=2206, tick_steps=400, overload=True,
-            wave=WAVE_BATCH):
+            wave=WAVE_BATCH, overload_storages=()):
     """Continuous batching against one-at-a-time float32 runs on the same
     seeded trace, offered at `load` x the sequential capacity (measured on
     three median-size requests of the trace): the arrival times are Poisson
     at that rate.  With `overload`, both arms also run the trace with every
     request arriving at t = 0, which shows capacity (aggregate MLUPS) rather
-    than the arrival rate.  Returns the summaries, the trace description and
-    how far the batched results (in `storage`) lie from the float32 ones."""
+    than the arrival rate; `overload_storages` adds batched arms in other
+    storages to that run.  Returns the summaries, the trace description and
+    how far the batched results lie from the float32 ones."""
     reqs = make_requests(n_req=n_req, seed=seed, L_min=L_min, L_max=L_max,
                          steps_min=steps_min, steps_max=steps_max, base_n=L_max)
     out = {}
     if overload:
         for r in reqs:
             r.arrival = 0.0
-        seq0 = summarize(run_sequential(reqs, wave=wave))
-        srv0 = Server(storage=storage, tick_steps=tick_steps, wave=wave)
-        bat0 = summarize(srv0.run(reqs))
-        bat0.update(storage=storage, graph_launches=srv0.graph_launches,
-                    captures=srv0.captures, ticks=srv0.ticks)
+        seq0_res = run_sequential(reqs, wave=wave)
+        seq0 = summarize(seq0_res)
         seq0.update(storage="f32")
-        out["overload"] = {"batched": bat0, "sequential": seq0,
-                           "arrivals": "all requests at t = 0"}
+        out["overload"] = {"sequential": seq0, "arrivals": "all requests at t = 0"}
+        for k, st in enumerate((storage,) + tuple(x for x in overload_storages if x != storage)):
+            srv0 = Server(storage=st, tick_steps=tick_steps, wave=wave)
+            res0 = srv0.run(reqs)
+            bat0 = summarize(res0)
+            bat0.update(storage=st, graph_launches=srv0.graph_launches,
+                        captures=srv0.captures, ticks=srv0.ticks,
+                        vs_sequential_f32=result_differences(res0, seq0_res))
+            out["overload"]["batched" if k == 0 else f"batched_{st}"] = bat0
     work = [r.nodes * r.steps for r in reqs]
     probe = sorted(reqs, key=lambda r: r.nodes)[len(reqs) // 2 - 1: len(reqs) // 2 + 2]
     for r in probe:
