@@ -321,18 +321,18 @@ def run_reference(args, world, rank):
 
 
 def serving_leg(args):
-    """Continuous batching (half-offset storage, the two batched passes per
-    step over the batch, CUDA graphs) against one-at-a-time float32 runs
+    """Continuous batching (local half-offset storage, the two batched passes
+    per step over the batch, CUDA graphs) against one-at-a-time float32 runs
     (two passes each) on the same seeded trace of heterogeneous requests:
     the trace shape of the serving workload (cubic L log-uniform in [32,
     192]) with fewer requests and step budgets scaled down, offered at 0.9
     of the sequential capacity and with every request arriving at once; the
-    capacity run also serves the local-offset storage (f16l)."""
+    capacity run also serves the faster half offsets from a constant (f16)."""
     from paper_2206_11524_gb300 import serve
     out = serve.compare(n_req=args.serve_requests, L_min=32, L_max=args.serve_lmax,
                         steps_min=args.serve_steps_min, steps_max=args.serve_steps_max,
                         storage=args.serve_storage, load=0.9, seed=2206, overload=True,
-                        overload_storages=("f16l",))
+                        overload_storages=("f16",))
     out["config"] = (f"{args.serve_requests} requests, L in [32, {args.serve_lmax}], steps "
                      f"U{{{args.serve_steps_min}..{args.serve_steps_max}}} (the 5,000-40,000 "
                      f"of the full trace scaled by {args.serve_steps_max / 40000:.3g})")
@@ -712,7 +712,7 @@ def main(argv=None):
     ap.add_argument("--serve-lmax", type=int, default=192)
     ap.add_argument("--serve-steps-min", type=int, default=312)
     ap.add_argument("--serve-steps-max", type=int, default=2500)
-    ap.add_argument("--serve-storage", default="f16")
+    ap.add_argument("--serve-storage", default="f16l")
     ap.add_argument("--storages", default="f32,f16,f16l",
                     help="storages whose two-pass step is timed on the same lattice "
                          "(comma list; '' skips)")

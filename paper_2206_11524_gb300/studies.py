@@ -414,7 +414,7 @@ def main(argv=None):
     c.add_argument("--lmax", type=int, default=192)
     c.add_argument("--steps-min", type=int, default=5000)
     c.add_argument("--steps-max", type=int, default=40000)
-    c.add_argument("--storage", default="f16")
+    c.add_argument("--storage", default="f16l")
     c.add_argument("--load", type=float, default=0.9)
     c.add_argument("--out", default="")
     args = ap.parse_args(argv)
