@@ -292,9 +292,13 @@ LBM_API lbm_status lbm_get_launch_config(const lbm_ctx *ctx, int *density_cfg,
  * state set) advance together, whatever their sizes and AA parities: when
  * every context uses the wavefront step (lbm_set_wavefront), each step is
  * one persistent wavefront launch over the tiles of all the lattices at
- * each AA parity present (in the first context's shape and lag); otherwise
- * one density launch and one fused launch cover every lattice.  Each
- * lattice computes exactly what lbm_step computes for it alone.  Work goes
+ * each AA parity present (in the first context's shape and lag; the
+ * lattices are numbered group by group in sets whose planes in flight fit
+ * half of L2); otherwise one density launch covers every lattice, and the
+ * fused pass is one launch per AA parity present in the first context's
+ * fused-pass shapes (the prefetching shapes 5..9 of lbm_set_launch_config;
+ * with another shape, one plain launch over every lattice).  Each lattice
+ * computes exactly what lbm_step computes for it alone.  Work goes
  * on `cuda_stream`; the contexts' own streams are not used, so the caller
  * orders the batch after earlier work on them.  EINVAL: bad count, NULL or
  * repeated context, mixed storage; ESTATE: a context without geometry or

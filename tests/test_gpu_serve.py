@@ -175,3 +175,27 @@ def test_sequential_baseline_runs():
                                steps_max=20, base_n=32)
     res = serve.run_sequential(reqs)
     assert len(res) == 2 and all(r.observables["nonfinite"] == 0 for r in res)
+
+
+def test_wave_batch_split_into_sets_equals_single_steps():
+    """Lattices whose planes in flight do not fit half of L2 together (two
+    256 x 260 / 256 x 272 planes need ~60 MB each at lag 4) go to separate
+    sets of the batched wavefront launch; with a small lattice beside them
+    and AA parities that differ, every population equals the lattices
+    stepped alone with two passes."""
+    shapes = ((5, 9, 40), (4, 260, 256), (3, 272, 256))
+    alone = _lattices("f32", shapes=shapes)
+    mixed = _lattices("f32", shapes=shapes, wave=2)
+    for g in alone:
+        g.step(5)
+    stream = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    lbm.lbm_batch_step([g.ctx for g in mixed], 2, stream.cuda_stream)
+    lbm.lbm_batch_step([mixed[1].ctx], 1, stream.cuda_stream)
+    lbm.lbm_batch_step([g.ctx for g in mixed], 2, stream.cuda_stream)
+    lbm.lbm_batch_step([g.ctx for k, g in enumerate(mixed) if k != 1], 1, stream.cuda_stream)
+    stream.synchronize()
+    for a, b in zip(alone, mixed):
+        assert a.t == b.t == 5
+        assert np.array_equal(a.populations(), b.populations())
+        assert lbm.lbm_fault_word(b.ctx) == 0
