@@ -324,8 +324,8 @@ def serving_leg(args):
     """Continuous batching (local half-offset storage, the two batched passes
     per step over the batch, CUDA graphs) against one-at-a-time float32 runs
     (two passes each) on the same seeded trace of heterogeneous requests:
-    the trace shape of the serving workload (cubic L log-uniform in [32,
-    192]) with fewer requests and step budgets scaled down, offered at 0.9
+    the trace of the serving workload (256 requests, cubic L log-uniform in
+    [32, 192]) with the step budgets scaled down, offered at 0.9
     of the sequential capacity and with every request arriving at once; the
     capacity run also serves the faster half offsets from a constant (f16)."""
     from paper_2206_11524_gb300 import serve
@@ -708,10 +708,10 @@ def main(argv=None):
                     help="time the single-pass step with boxes of about this many planes")
     ap.add_argument("--launch-config", default="",
                     help="density,even,odd launch shapes (skips the autotuner)")
-    ap.add_argument("--serve-requests", type=int, default=64)
+    ap.add_argument("--serve-requests", type=int, default=256)
     ap.add_argument("--serve-lmax", type=int, default=192)
-    ap.add_argument("--serve-steps-min", type=int, default=312)
-    ap.add_argument("--serve-steps-max", type=int, default=2500)
+    ap.add_argument("--serve-steps-min", type=int, default=156)
+    ap.add_argument("--serve-steps-max", type=int, default=1250)
     ap.add_argument("--serve-storage", default="f16l")
     ap.add_argument("--storages", default="f32,f16,f16l",
                     help="storages whose two-pass step is timed on the same lattice "

@@ -42,13 +42,15 @@ void collide_pipe_launch(const StepParams &p, const Workspace &w, cudaStream_t s
   constexpr Shape S = CollideShape<PARITY, kST, CFG>::s;
   constexpr PipeCfg P = pipe_cfg(CFG);
   constexpr int smem = pipe_smem_bytes(CFG, (int)sizeof(T2), PC);
-  static bool attr_set = false;
-  if (!attr_set) {
-    if (cudaFuncSetAttribute(k_collide_pipe<PARITY, kST, PC, CFG>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
-      return;  // the launch below then reports the error
-    attr_set = true;
-  }
+  // the shared-memory limit is an attribute of the function on each device;
+  // if setting it fails, the launch below reports the error
+  static std::once_flag attr_once[16];
+  int dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < 16)
+    std::call_once(attr_once[dev], [] {
+      cudaFuncSetAttribute(k_collide_pipe<PARITY, kST, PC, CFG>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    });
   const dim3 grid(p.ntx, (p.ny + S.by - 1) / S.by, (p.nz + P.zc - 1) / P.zc);
   k_collide_pipe<PARITY, kST, PC, CFG><<<grid, dim3(kTile, S.by, 1), smem, s>>>(p, w);
 }
@@ -386,13 +388,18 @@ cudaError_t batch_pipe_launch(const BatchArgs &a, cudaStream_t s) {
     ++b.n;
   }
   if (b.n == 0) return cudaSuccess;
-  static std::once_flag attr_once;
-  static cudaError_t attr_err = cudaSuccess;
-  std::call_once(attr_once, [] {
-    attr_err = cudaFuncSetAttribute(k_batch_collide_pipe<PARITY, kST, PC, CFG>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  // the shared-memory limit is an attribute of the function on each device
+  static std::once_flag attr_once[16];
+  static cudaError_t attr_err[16];
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 16) return cudaErrorInvalidDevice;
+  std::call_once(attr_once[dev], [dev] {
+    attr_err[dev] = cudaFuncSetAttribute(k_batch_collide_pipe<PARITY, kST, PC, CFG>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   });
-  if (attr_err != cudaSuccess) return attr_err;
+  if (attr_err[dev] != cudaSuccess) return attr_err[dev];
   k_batch_collide_pipe<PARITY, kST, PC, CFG>
       <<<(unsigned)b.prefix[b.n], dim3(kTile, S.by, 1), smem, s>>>(b);
   return cudaGetLastError();
