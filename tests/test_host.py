@@ -140,3 +140,44 @@ def test_serving_result_differences():
     assert abs(d["sat1_abs_median"] - 0.001) < 1e-12
     assert abs(d["mass_rel_max"] - 0.1) < 1e-12
     assert abs(d["mass_rel_median"] - 0.005) < 1e-12
+
+
+def test_traffic_recorder_reads_ncu_csv(tmp_path, monkeypatch):
+    """bench.py --record-traffic: per-launch DRAM bytes of the named kernel
+    only (not k_wave_batch), units scaled, the mean per node written with the
+    hash of the device code into the profile's machine-readable lines."""
+    import bench
+    hdr = ('"ID","Process ID","Process Name","Host Name","Kernel Name","Context","Stream",'
+           '"Block Size","Grid Size","Device","CC","Section Name","Metric Name","Metric Unit",'
+           '"Metric Value"\n')
+
+    def row(i, name, metric, unit, value):
+        return (f'"{i}","1","python","h","{name}","1","7","(32, 2, 1)","(1216, 1, 1)","0",'
+                f'"10.3","Command line profiler metrics","{metric}","{unit}","{value}"\n')
+    kw = "void unnamed>::k_wave<1, 0, 0, 2>(StepParams, Workspace, unnamed>::WaveArgs)"
+    kb = "void unnamed>::k_wave_batch<1, 0, 0, 2>(unnamed>::WaveBatch)"
+    csv = tmp_path / "t.csv"
+    csv.write_text("==PROF== Connected\n" + hdr +
+                   row(0, kw, "dram__bytes_read.sum", "Gbyte", "3.0") +
+                   row(0, kw, "dram__bytes_write.sum", "byte", "1,000,000,000") +
+                   row(0, kw, "gpu__time_duration.sum", "ns", "1,200,000") +
+                   row(1, kb, "dram__bytes_read.sum", "byte", "99") +
+                   row(1, kb, "dram__bytes_write.sum", "byte", "99") +
+                   row(2, kw, "dram__bytes_read.sum", "Mbyte", "1000") +
+                   row(2, kw, "dram__bytes_write.sum", "Kbyte", "1000000") +
+                   row(2, kw, "gpu__time_duration.sum", "us", "1100"))
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    (prof / "wave_electrode256.md").write_text("# summary\n\nkernel_source_sha256_16: old\n"
+                                               "dram_bytes_per_node: 1.0\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "_kernel_sha", lambda: "abc")
+    rows, bpn = bench.record_traffic(str(csv), "k_wave", 1000)
+    assert [r["id"] for r in rows] == [0, 2]
+    assert abs(rows[0]["total_per_node"] - 4.0e6) < 1e-6
+    assert abs(rows[1]["total_per_node"] - 2.0e6) < 1e-6
+    assert abs(rows[0]["us"] - 1200.0) < 1e-9 and abs(rows[1]["us"] - 1100.0) < 1e-9
+    assert bpn == 3.0e6
+    text = (prof / "wave_electrode256.md").read_text()
+    assert "kernel_source_sha256_16: abc" in text and "dram_bytes_per_node: 3000000.00" in text
+    assert text.count("kernel_source_sha256_16") == 1 and text.startswith("# summary")
