@@ -357,7 +357,7 @@ def compare(n_req=24, L_min=32, L_max=160, steps_min=1000, steps_max=6000,
     at that rate.  With `overload`, both arms also run the trace with every
     request arriving at t = 0, which shows capacity (aggregate MLUPS) rather
     than the arrival rate; `overload_storages` adds batched arms in other
-    storages to that run.  Returns the summaries, the trace description and
+    storages to that run.  load = 0 runs the capacity run only.  Returns the summaries, the trace description and
     how far the batched results lie from the float32 ones."""
     reqs = make_requests(n_req=n_req, seed=seed, L_min=L_min, L_max=L_max,
                          steps_min=steps_min, steps_max=steps_max, base_n=L_max)
@@ -377,6 +377,8 @@ def compare(n_req=24, L_min=32, L_max=160, steps_min=1000, steps_max=6000,
                         captures=srv0.captures, ticks=srv0.ticks,
                         vs_sequential_f32=result_differences(res0, seq0_res))
             out["overload"]["batched" if k == 0 else f"batched_{st}"] = bat0
+    if not load:        # capacity run only
+        return out
     work = [r.nodes * r.steps for r in reqs]
     probe = sorted(reqs, key=lambda r: r.nodes)[len(reqs) // 2 - 1: len(reqs) // 2 + 2]
     for r in probe:
