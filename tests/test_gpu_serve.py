@@ -97,7 +97,7 @@ def _lattices(storage, shapes=((20, 12, 40), (8, 30, 64), (17, 9, 33)), wave=0):
 
 
 @pytest.mark.parametrize("wave", [0, 2])
-@pytest.mark.parametrize("storage", ["f32", "f16", "f16l"])
+@pytest.mark.parametrize("storage", ["f32", "f16", "f16l", "bf16", "bf16l"])
 def test_batch_step_equals_single_steps(storage, wave):
     """Batched steps equal single steps bit for bit, also while the
     lattices of one batched call are at different AA parities (one launch
@@ -175,6 +175,28 @@ def test_sequential_baseline_runs():
                                steps_max=20, base_n=32)
     res = serve.run_sequential(reqs)
     assert len(res) == 2 and all(r.observables["nonfinite"] == 0 for r in res)
+
+
+def test_compare_reports_capacity_and_arrival_arms():
+    """The serving comparison on a tiny trace: the capacity run with a
+    second batched storage and the arrival run, every request answered in
+    every arm, and each batched result set beside its float32 one (the
+    local-offset storage stays close on so few steps)."""
+    out = serve.compare(n_req=6, L_min=16, L_max=28, steps_min=8, steps_max=24,
+                        storage="f16l", load=0.9, seed=5, tick_steps=8,
+                        overload_storages=("f16",))
+    ov = out["overload"]
+    for arm in ("sequential", "batched", "batched_f16"):
+        assert ov[arm]["requests"] == 6 and ov[arm]["mlups"] > 0
+    assert ov["batched"]["storage"] == "f16l" and ov["batched_f16"]["storage"] == "f16"
+    for arm in ("batched", "sequential"):
+        assert out[arm]["requests"] == 6
+        assert out[arm]["p99_s"] >= out[arm]["p50_s"] > 0
+    d = out["batched_vs_sequential_f32"]
+    assert d["sat1_abs_max"] < 1e-2 and d["mass_rel_max"] < 1e-2
+    assert ov["batched"]["vs_sequential_f32"]["mass_rel_max"] < 1e-2
+    assert serve.compare(n_req=2, L_min=16, L_max=16, steps_min=4, steps_max=4,
+                         load=0, seed=6, tick_steps=4).keys() == {"overload"}
 
 
 def test_wave_batch_split_into_sets_equals_single_steps():
